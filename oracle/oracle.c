@@ -1,0 +1,627 @@
+/*
+ * oracle.c — plain CPU oracle for the weighted-Hamming search path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call this code:
+ * only the tests, the package's smoke check and the benchmark's CPU-baseline
+ * leg use it.  It shares no code, header or table with the CUDA library.
+ *
+ * Written for clarity, not speed: single descriptors are handled one at a
+ * time, bits one at a time where the definition is per bit, FP64 for every
+ * real-valued quantity.  Each function names the passage of the paper
+ * (arXiv 2107.03368, "Partial 3D Object Retrieval using Local Binary QUICCI
+ * Descriptors and Dissimilarity Tree Indexing") that it follows.
+ *
+ * Readings of the paper taken here (the paper is silent, garbled or
+ * inconsistent at these points):
+ *   R1  Eq. 1's type-B denominator is max(N*N - |q|, 1): N*N bits can be of
+ *       type B at most (the text normalises by the errors that can occur).
+ *   R2  The node bound of §4.2 is used in Eq. 1's units with Eq. 1's guards:
+ *       scaled by P*Z it is popc(q & ~OR) * Z (+ popc(~q & AND) * P).
+ *   R3  The split loop of §4.1 stops right after the first bit (in ascending
+ *       popularity order, ties by bit index) whose move makes the dissimilar
+ *       set hold at least ceil(n/2) descriptors ("roughly equal" halves).
+ *   R4  If a split leaves either side empty, the node's list (ascending
+ *       original index) is cut by position: first floor(n/2) similar.
+ *   R5  A node is a leaf iff it holds at most leaf_size descriptors.
+ *   R5b Every node, leaves included, carries its OR (sum) image; the AND
+ *       (product) image is computed and used only when asked for.
+ *   R5c Nodes are numbered breadth first, the similar child before the
+ *       dissimilar one; each node's descriptors occupy a contiguous segment
+ *       of the permutation, similar part first, ascending original index.
+ *   R6  Best-first search runs while the queue is non-empty and the smallest
+ *       open bound does not exceed the current k-th result.
+ *   R7  A child is pruned only if its bound is strictly greater than the
+ *       k-th result, so equal-distance lower-index results are never lost.
+ *   R8  Results are ordered by (distance, original index) ascending.
+ *   R10 "At random" in the voting loop of §3 is a Fisher-Yates permutation
+ *       driven by SplitMix64; a vote goes to the object of the top-1 result.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OW 64          /* 64 words of 64 bits: a 64x64-bit QUICCI image (§6) */
+#define OBITS 4096
+
+/* ------------------------------------------------------------------------ */
+/* Bits                                                                      */
+/* ------------------------------------------------------------------------ */
+
+static int get_bit(const uint64_t *d, int b)
+{
+    return (int)((d[b >> 6] >> (b & 63)) & 1u);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 (§2.3): weighted Hamming distance                                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Eq. 1 for an N x N binary image given one byte per bit (row-major).
+ * Type A error: query bit 1, target bit 0.  Type B: query 0, target 1.
+ * delta = A / max(|q|, 1) + B / max(N*N - |q|, 1)   (reading R1).
+ */
+double orc_wh_bytes(const uint8_t *q, const uint8_t *t, int N, int32_t *A_out, int32_t *B_out)
+{
+    int sq = 0, a = 0, b = 0;
+    for (int r = 0; r < N; ++r)
+        for (int c = 0; c < N; ++c) {
+            int qb = q[r * N + c] ? 1 : 0, tb = t[r * N + c] ? 1 : 0;
+            sq += qb;
+            a += qb * (1 - tb);
+            b += (1 - qb) * tb;
+        }
+    double P = sq > 1 ? (double)sq : 1.0;
+    double Z = (N * N - sq) > 1 ? (double)(N * N - sq) : 1.0;
+    if (A_out) *A_out = a;
+    if (B_out) *B_out = b;
+    return (double)a / P + (double)b / Z;
+}
+
+/* Eq. 1 on a packed 64x64 descriptor, one bit at a time. */
+double orc_wh_bitwise(const uint64_t *q, const uint64_t *t, int32_t *A_out, int32_t *B_out)
+{
+    int sq = 0, a = 0, b = 0;
+    for (int i = 0; i < OBITS; ++i) {
+        int qb = get_bit(q, i), tb = get_bit(t, i);
+        sq += qb;
+        a += qb & (1 - tb);
+        b += (1 - qb) & tb;
+    }
+    double P = sq > 1 ? (double)sq : 1.0;
+    double Z = (OBITS - sq) > 1 ? (double)(OBITS - sq) : 1.0;
+    if (A_out) *A_out = a;
+    if (B_out) *B_out = b;
+    return (double)a / P + (double)b / Z;
+}
+
+/*
+ * The type A and type B error counts of Eq. 1 on packed words: A counts the
+ * positions set in q and clear in t, B the positions clear in q and set in t
+ * (a library popcount counts the bits of each masked word).
+ */
+static void error_counts(const uint64_t *q, const uint64_t *t, int *a, int *b)
+{
+    int sa = 0, sb = 0;
+    for (int w = 0; w < OW; ++w) {
+        sa += __builtin_popcountll(q[w] & ~t[w]);
+        sb += __builtin_popcountll(~q[w] & t[w]);
+    }
+    *a = sa;
+    *b = sb;
+}
+
+/* Same value as orc_wh_bitwise, word at a time (used for the large scans). */
+double orc_wh(const uint64_t *q, const uint64_t *t, int32_t *A_out, int32_t *B_out)
+{
+    int sq = 0, a, b;
+    for (int w = 0; w < OW; ++w) sq += __builtin_popcountll(q[w]);
+    error_counts(q, t, &a, &b);
+    double P = sq > 1 ? (double)sq : 1.0;
+    double Z = (OBITS - sq) > 1 ? (double)(OBITS - sq) : 1.0;
+    if (A_out) *A_out = a;
+    if (B_out) *B_out = b;
+    return (double)a / P + (double)b / Z;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ranked result lists (reading R8)                                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For one query, P = max(|q|,1) and Z = max(4096-|q|,1) are fixed, so
+ * comparing two Eq. 1 values a1/P + b1/Z and a2/P + b2/Z exactly is the same
+ * as comparing a1*Z + b1*P and a2*Z + b2*P (both sides multiplied by P*Z>0).
+ * The oracle compares these exact integers, never the rounded doubles.
+ */
+typedef struct { int64_t num; int64_t idx; int32_t a, b; } result_t;
+
+static int res_less(const result_t *x, const result_t *y)
+{
+    if (x->num != y->num) return x->num < y->num;
+    return x->idx < y->idx;
+}
+
+/* Insert r into the sorted list res[0..*len) capped at k entries. */
+static void res_insert(result_t *res, int *len, int k, result_t r)
+{
+    if (*len == k && !res_less(&r, &res[k - 1])) return;
+    int i = (*len < k) ? (*len)++ : k - 1;
+    while (i > 0 && res_less(&r, &res[i - 1])) {
+        res[i] = res[i - 1];
+        --i;
+    }
+    res[i] = r;
+}
+
+static void res_write(const result_t *res, int len, int k, int64_t P, int64_t Z,
+                      int64_t *idx, double *score, int32_t *ab)
+{
+    for (int j = 0; j < k; ++j) {
+        if (j < len) {
+            idx[j] = res[j].idx;
+            score[j] = (double)res[j].a / (double)P + (double)res[j].b / (double)Z;
+            if (ab) { ab[2 * j] = res[j].a; ab[2 * j + 1] = res[j].b; }
+        } else {           /* fewer than k descriptors exist */
+            idx[j] = -1;
+            score[j] = INFINITY;
+            if (ab) { ab[2 * j] = -1; ab[2 * j + 1] = -1; }
+        }
+    }
+}
+
+static void query_weights(const uint64_t *q, int64_t *P, int64_t *Z)
+{
+    int sq = 0;
+    for (int w = 0; w < OW; ++w) sq += __builtin_popcountll(q[w]);
+    *P = sq > 1 ? sq : 1;
+    *Z = (OBITS - sq) > 1 ? (OBITS - sq) : 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sequential search (§6.2): every database descriptor against the query    */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For each of nq queries, the k database descriptors with the smallest Eq. 1
+ * distance, ties by lowest index.  Outputs idx[nq][k] (-1 past n), score
+ * [nq][k] (FP64 Eq. 1, +inf past n), ab[nq][k][2] = (A, B) (nullable).
+ */
+void orc_bf_topk(const uint64_t *db, int64_t n, const uint64_t *qs, int64_t nq, int32_t k,
+                 int64_t *idx, double *score, int32_t *ab, int32_t nthreads)
+{
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        const uint64_t *q = qs + qi * OW;
+        int64_t P, Z;
+        query_weights(q, &P, &Z);
+        result_t *res = (result_t *)malloc(sizeof(result_t) * (size_t)k);
+        int len = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            int a, b;
+            error_counts(q, db + i * OW, &a, &b);
+            result_t r = { (int64_t)a * Z + (int64_t)b * P, i, a, b };
+            res_insert(res, &len, k, r);
+        }
+        res_write(res, len, k, P, Z, idx + qi * k, score + qi * k, ab ? ab + qi * k * 2 : NULL);
+        free(res);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dissimilarity Tree construction (§4.1, construction listing)             */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Flattened tree written by both builders (reading R5c):
+ *   child[2*i], child[2*i+1]  similar / dissimilar child of node i, -1 at a leaf
+ *   begin[i], count[i]        node i's segment of perm
+ *   level[i]                  depth of node i (root 0)
+ *   or_img[i*64..]            OR (sum) image of node i's descriptors
+ *   and_img[i*64..]           AND (product) image (nullable)
+ *   perm[n]                   tree position -> original index
+ * Capacities: nodes <= 2n-1 (n >= 1).  Returns the node count.
+ */
+typedef struct {
+    int64_t *child, *begin, *count;
+    int32_t *level;
+    uint64_t *or_img, *and_img;
+    int64_t *perm;
+} orc_tree_out;
+
+typedef struct { int64_t node, begin, count; int32_t level; } work_t;
+
+typedef struct { int64_t count; int bit; } bitkey_t;
+
+static int cmp_bitkey(const void *x, const void *y)
+{
+    const bitkey_t *a = (const bitkey_t *)x, *b = (const bitkey_t *)y;
+    if (a->count != b->count) return a->count < b->count ? -1 : 1;
+    return (a->bit > b->bit) - (a->bit < b->bit);
+}
+
+/* Split rule of the literal listing: returns the number of similar
+ * descriptors and reorders list[0..n) as similar then dissimilar, each part
+ * keeping ascending original index. */
+static int64_t split_literal(const uint64_t *db, int64_t *list, int64_t n)
+{
+    /* popularity of every bit over the node's descriptors (§4.1) */
+    int64_t *counts = (int64_t *)calloc(OBITS, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i)
+        for (int b = 0; b < OBITS; ++b)
+            counts[b] += get_bit(db + list[i] * OW, b);
+    /* bitOrder: ascending popularity, ties by bit index (reading R3) */
+    bitkey_t *order = (bitkey_t *)malloc(sizeof(bitkey_t) * OBITS);
+    for (int b = 0; b < OBITS; ++b) order[b] = (bitkey_t){ counts[b], b };
+    qsort(order, OBITS, sizeof(bitkey_t), cmp_bitkey);
+    /* move every similar descriptor with the current bit set, bit by bit,
+     * until the dissimilar set holds at least ceil(n/2) (reading R3) */
+    char *in_similar = (char *)malloc((size_t)n);
+    memset(in_similar, 1, (size_t)n);
+    int64_t n_dis = 0, target = (n + 1) / 2;
+    for (int r = 0; r < OBITS && n_dis < target; ++r) {
+        int b = order[r].bit;
+        for (int64_t i = 0; i < n; ++i)
+            if (in_similar[i] && get_bit(db + list[i] * OW, b)) {
+                in_similar[i] = 0;
+                ++n_dis;
+            }
+    }
+    int64_t n_sim = n - n_dis;
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t s = 0, d = n_sim;
+    if (n_sim == 0 || n_dis == 0) {            /* reading R4 */
+        n_sim = n / 2;
+        memcpy(tmp, list, sizeof(int64_t) * (size_t)n);
+    } else {
+        for (int64_t i = 0; i < n; ++i) {
+            if (in_similar[i]) tmp[s++] = list[i];
+            else tmp[d++] = list[i];
+        }
+    }
+    memcpy(list, tmp, sizeof(int64_t) * (size_t)n);
+    free(tmp);
+    free(in_similar);
+    free(order);
+    free(counts);
+    return n_sim;
+}
+
+static int cmp_u64(const void *x, const void *y)
+{
+    uint64_t a = *(const uint64_t *)x, b = *(const uint64_t *)y;
+    return a < b ? -1 : a > b;
+}
+
+/*
+ * The same split in closed form.  Give bit b the key (popularity(b), b); the
+ * position of b in bitOrder is the rank of its key.  After the listing has
+ * processed the first r+1 bits of bitOrder, the dissimilar set is exactly
+ * the descriptors whose smallest set-bit key is at most the key of bit r.
+ * So the loop stops at the ceil(n/2)-th smallest of these per-descriptor
+ * minima, K*, and dissimilar = {d : minkey(d) <= K*} (all non-empty
+ * descriptors if fewer than ceil(n/2) exist).  Counting only the set bits
+ * makes it fast enough for millions of descriptors.
+ */
+static int64_t split_minrank(const uint64_t *db, int64_t *list, int64_t n)
+{
+    int64_t *counts = (int64_t *)calloc(OBITS, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) {
+        const uint64_t *d = db + list[i] * OW;
+        for (int w = 0; w < OW; ++w) {
+            uint64_t x = d[w];
+            while (x) {
+                counts[w * 64 + __builtin_ctzll(x)]++;
+                x &= x - 1;
+            }
+        }
+    }
+    const uint64_t NONE = UINT64_MAX;
+    uint64_t *mk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    uint64_t *sorted = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const uint64_t *d = db + list[i] * OW;
+        uint64_t m = NONE;
+        for (int w = 0; w < OW; ++w) {
+            uint64_t x = d[w];
+            while (x) {
+                int b = w * 64 + __builtin_ctzll(x);
+                uint64_t key = ((uint64_t)counts[b] << 12) | (uint64_t)b;
+                if (key < m) m = key;
+                x &= x - 1;
+            }
+        }
+        mk[i] = sorted[i] = m;
+    }
+    qsort(sorted, (size_t)n, sizeof(uint64_t), cmp_u64);
+    int64_t target = (n + 1) / 2;
+    int64_t n_finite = 0;
+    while (n_finite < n && sorted[n_finite] != NONE) ++n_finite;
+    uint64_t kstar = n_finite >= target ? sorted[target - 1]
+                   : (n_finite > 0 ? sorted[n_finite - 1] : 0);
+    int64_t n_dis = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (mk[i] != NONE && mk[i] <= kstar) ++n_dis;
+    int64_t n_sim = n - n_dis;
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (n_sim == 0 || n_dis == 0) {            /* reading R4 */
+        n_sim = n / 2;
+    } else {
+        int64_t s = 0, d = n_sim;
+        for (int64_t i = 0; i < n; ++i) {
+            if (mk[i] != NONE && mk[i] <= kstar) tmp[d++] = list[i];
+            else tmp[s++] = list[i];
+        }
+        memcpy(list, tmp, sizeof(int64_t) * (size_t)n);
+    }
+    free(tmp);
+    free(sorted);
+    free(mk);
+    free(counts);
+    return n_sim;
+}
+
+static void node_images(const uint64_t *db, const int64_t *list, int64_t n,
+                        uint64_t *or_img, uint64_t *and_img)
+{
+    for (int w = 0; w < OW; ++w) {
+        uint64_t o = 0, a = n > 0 ? ~0ULL : 0;
+        for (int64_t i = 0; i < n; ++i) {
+            o |= db[list[i] * OW + w];
+            a &= db[list[i] * OW + w];
+        }
+        or_img[w] = o;
+        if (and_img) and_img[w] = a;
+    }
+}
+
+/*
+ * Builds the tree breadth first (a FIFO of pending nodes); the recursion of
+ * the listing visits the same nodes with the same splits, only in another
+ * order.  literal != 0 selects the bit-by-bit move loop, else the closed
+ * form.  Returns the number of nodes.
+ */
+int64_t orc_build(const uint64_t *db, int64_t n, int32_t leaf_size, int32_t literal,
+                  int64_t *child, int64_t *begin, int64_t *count, int32_t *level,
+                  uint64_t *or_img, uint64_t *and_img, int64_t *perm)
+{
+    if (n <= 0) return 0;
+    for (int64_t i = 0; i < n; ++i) perm[i] = i;
+    int64_t cap = 2 * n;
+    work_t *queue = (work_t *)malloc(sizeof(work_t) * (size_t)cap);
+    int64_t head = 0, tail = 0, next_id = 1;
+    queue[tail++] = (work_t){ 0, 0, n, 0 };
+    while (head < tail) {
+        work_t w = queue[head++];
+        int64_t *list = perm + w.begin;
+        begin[w.node] = w.begin;
+        count[w.node] = w.count;
+        level[w.node] = w.level;
+        node_images(db, list, w.count, or_img + w.node * OW,
+                    and_img ? and_img + w.node * OW : NULL);
+        if (w.count <= leaf_size) {            /* reading R5 */
+            child[2 * w.node] = child[2 * w.node + 1] = -1;
+            continue;
+        }
+        int64_t n_sim = literal ? split_literal(db, list, w.count)
+                                : split_minrank(db, list, w.count);
+        int64_t s = next_id++, d = next_id++;
+        child[2 * w.node] = s;
+        child[2 * w.node + 1] = d;
+        queue[tail++] = (work_t){ s, w.begin, n_sim, w.level + 1 };
+        queue[tail++] = (work_t){ d, w.begin + n_sim, w.count - n_sim, w.level + 1 };
+    }
+    free(queue);
+    return next_id;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dissimilarity Tree query (§4.2, query listing)                            */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Lower bound of Eq. 1 (times P*Z) over every descriptor below a node
+ * (§4.2, reading R2): a query bit that is 0 in the node's OR image is a type
+ * A error for every descriptor below; a query 0 bit set in the AND image is
+ * a type B error for all of them.
+ */
+static int64_t node_bound(const uint64_t *q, const uint64_t *or_img, const uint64_t *and_img,
+                          int64_t P, int64_t Z)
+{
+    int64_t a = 0, b = 0;
+    for (int i = 0; i < OBITS; ++i) {
+        int qb = get_bit(q, i);
+        if (qb && !get_bit(or_img, i)) ++a;
+        if (and_img && !qb && get_bit(and_img, i)) ++b;
+    }
+    return a * Z + b * P;
+}
+
+int64_t orc_node_bound(const uint64_t *q, const uint64_t *or_img, const uint64_t *and_img)
+{
+    int64_t P, Z;
+    query_weights(q, &P, &Z);
+    return node_bound(q, or_img, and_img, P, Z);
+}
+
+typedef struct { int64_t bound, node; } open_t;
+
+static int open_less(const open_t *x, const open_t *y)
+{
+    if (x->bound != y->bound) return x->bound < y->bound;
+    return x->node < y->node;
+}
+
+/* binary min-heap of open nodes */
+static void heap_push(open_t *h, int64_t *len, open_t v)
+{
+    int64_t i = (*len)++;
+    h[i] = v;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!open_less(&h[i], &h[p])) break;
+        open_t t = h[i]; h[i] = h[p]; h[p] = t;
+        i = p;
+    }
+}
+
+static open_t heap_pop(open_t *h, int64_t *len)
+{
+    open_t top = h[0];
+    h[0] = h[--(*len)];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, m = i;
+        if (l < *len && open_less(&h[l], &h[m])) m = l;
+        if (r < *len && open_less(&h[r], &h[m])) m = r;
+        if (m == i) break;
+        open_t t = h[i]; h[i] = h[m]; h[m] = t;
+        i = m;
+    }
+    return top;
+}
+
+/*
+ * Best-first search for the k nearest descriptors (readings R6-R8).
+ * stats[nq][4] (nullable) = nodes popped, leaves scanned, descriptors
+ * scanned, bounds evaluated.
+ */
+void orc_tree_search(const uint64_t *db, int64_t n_nodes, const int64_t *child,
+                     const int64_t *begin, const int64_t *count, const uint64_t *or_img,
+                     const uint64_t *and_img, const int64_t *perm, const uint64_t *qs, int64_t nq,
+                     int32_t k, int64_t *idx, double *score, int32_t *ab, int64_t *stats,
+                     int32_t nthreads)
+{
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int64_t qi = 0; qi < nq; ++qi) {
+        const uint64_t *q = qs + qi * OW;
+        int64_t P, Z;
+        query_weights(q, &P, &Z);
+        result_t *res = (result_t *)malloc(sizeof(result_t) * (size_t)k);
+        int len = 0;
+        open_t *heap = (open_t *)malloc(sizeof(open_t) * (size_t)(n_nodes + 1));
+        int64_t hlen = 0, popped = 0, leaves = 0, scanned = 0, bounds = 0;
+        if (n_nodes > 0) {
+            heap_push(heap, &hlen, (open_t){ node_bound(q, or_img, and_img, P, Z), 0 });
+            ++bounds;
+        }
+        while (hlen > 0) {
+            int64_t worst = len < k ? INT64_MAX : res[k - 1].num;
+            if (heap[0].bound > worst) break;  /* reading R6 */
+            open_t cur = heap_pop(heap, &hlen);
+            ++popped;
+            int64_t nd = cur.node;
+            if (child[2 * nd] < 0) {           /* leaf: exact distances */
+                ++leaves;
+                for (int64_t j = 0; j < count[nd]; ++j) {
+                    int64_t orig = perm[begin[nd] + j];
+                    int a, b;
+                    error_counts(q, db + orig * OW, &a, &b);
+                    result_t r = { (int64_t)a * Z + (int64_t)b * P, orig, a, b };
+                    res_insert(res, &len, k, r);
+                    ++scanned;
+                }
+            } else {
+                for (int c = 0; c < 2; ++c) {
+                    int64_t ch = child[2 * nd + c];
+                    int64_t lb = node_bound(q, or_img + ch * OW,
+                                            and_img ? and_img + ch * OW : NULL, P, Z);
+                    ++bounds;
+                    int64_t w2 = len < k ? INT64_MAX : res[k - 1].num;
+                    if (lb <= w2) heap_push(heap, &hlen, (open_t){ lb, ch });  /* R7 */
+                }
+            }
+        }
+        res_write(res, len, k, P, Z, idx + qi * k, score + qi * k, ab ? ab + qi * k * 2 : NULL);
+        if (stats) {
+            stats[qi * 4 + 0] = popped;
+            stats[qi * 4 + 1] = leaves;
+            stats[qi * 4 + 2] = scanned;
+            stats[qi * 4 + 3] = bounds;
+        }
+        free(heap);
+        free(res);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Voting pipeline (§3)                                                      */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 (Steele, Lea & Flood 2014): state += gamma, then mix. */
+uint64_t orc_splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/*
+ * The random order in which query j's n descriptors are drawn (reading R10):
+ * the generator is SplitMix64 seeded with the (j+1)-th output of SplitMix64
+ * seeded with `seed`; Fisher-Yates (Durstenfeld) from the last position down,
+ * swapping position i with position (draw mod (i+1)).
+ */
+void orc_permutation(uint64_t seed, int64_t j, int64_t n, int64_t *out)
+{
+    uint64_t s0 = seed + (uint64_t)j * 0x9e3779b97f4a7c15ULL;
+    uint64_t state = orc_splitmix64_next(&s0);
+    for (int64_t i = 0; i < n; ++i) out[i] = i;
+    for (int64_t i = n - 1; i > 0; --i) {
+        uint64_t r = orc_splitmix64_next(&state) % (uint64_t)(i + 1);
+        int64_t t = out[i]; out[i] = out[(int64_t)r]; out[(int64_t)r] = t;
+    }
+}
+
+/*
+ * Partial-object retrieval (§3): for query j, draw its descriptors in the
+ * random order above, find each one's nearest database descriptor (top-1 by
+ * sequential search), vote for that descriptor's object, and stop when an
+ * object reaches `threshold` votes (threshold 0: use every descriptor).
+ * The winner is the first object to reach the threshold, else the object
+ * with most votes (lowest id on ties), -1 when no vote was cast.
+ * votes[nq][n_objects] = the votes cast, consumed[nq] = descriptors used.
+ */
+void orc_retrieve(const uint64_t *db, int64_t n, const uint32_t *object_of, int32_t n_objects,
+                  const uint64_t *qdesc, const int64_t *offsets, int32_t nq, int32_t threshold,
+                  uint64_t seed, uint32_t *votes, int32_t *winner, int64_t *consumed,
+                  int32_t nthreads)
+{
+    for (int32_t j = 0; j < nq; ++j) {
+        int64_t m = offsets[j + 1] - offsets[j];
+        uint32_t *v = votes + (int64_t)j * n_objects;
+        memset(v, 0, sizeof(uint32_t) * (size_t)n_objects);
+        int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        int64_t *nn = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+        double *sc = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+        orc_permutation(seed, j, m, order);
+        /* nearest neighbour of every descriptor of the query (exact, so the
+         * order in which they are computed does not matter) */
+        if (m > 0)
+            orc_bf_topk(db, n, qdesc + offsets[j] * OW, m, 1, nn, sc, NULL, nthreads);
+        int32_t win = -1;
+        int64_t used = 0;
+        for (int64_t i = 0; i < m; ++i) {
+            int64_t t = nn[order[i]];
+            uint32_t o = object_of[t];
+            ++v[o];
+            ++used;
+            if (threshold > 0 && v[o] == (uint32_t)threshold) {
+                win = (int32_t)o;
+                break;
+            }
+        }
+        if (win < 0) {
+            uint32_t best = 0;
+            for (int32_t o = 0; o < n_objects; ++o)
+                if (v[o] > best) { best = v[o]; win = o; }
+        }
+        winner[j] = win;
+        consumed[j] = used;
+        free(sc);
+        free(nn);
+        free(order);
+    }
+}
