@@ -1,0 +1,211 @@
+/*
+ * dt.h — C ABI of libdt.so: weighted-Hamming nearest-neighbour search over
+ * 64x64-bit QUICCI descriptors, by brute force and through a Dissimilarity
+ * Tree, plus per-object voting for partial-object retrieval.
+ *
+ * The operations follow arXiv 2107.03368 (van Blokland & Theoharis,
+ * "Partial 3D Object Retrieval using Local Binary QUICCI Descriptors and
+ * Dissimilarity Tree Indexing"):
+ *   distance      Eq. 1 (§2.3), weighted Hamming distance
+ *   bf_search     sequential search (§6.2)
+ *   dt_build      Dissimilarity Tree construction (§4.1)
+ *   dt_search     Dissimilarity Tree query (§4.2)
+ *   retrieve_objects   the voting pipeline (§3)
+ *
+ * Common conventions
+ * ------------------
+ * Descriptor layout: 64 x uint64 = 4096 bits = 512 bytes, row-major; word r
+ *   holds layer r counted from the bottom, bit c of it the circle of radius
+ *   index c counted from the innermost (§2.2).  Descriptor arrays are
+ *   contiguous [count][64] uint64 and must be 16-byte aligned.
+ * Distance: for query q and target t, A = #(q=1, t=0), B = #(q=0, t=1),
+ *   P = max(|q|, 1), Z = max(4096 - |q|, 1) and delta = A/P + B/Z (Eq. 1,
+ *   with 4096 = N*N bits as the count of possible type B errors).
+ *   Results are ranked by the exact value of delta, i.e. by the integer
+ *   A*Z + B*P, ties by lowest database index.  Scores are FP32: delta
+ *   correctly rounded from the exact rational (A*Z + B*P) / (P*Z).
+ * Results: idx[nq][k] (uint32, original database index), score[nq][k]
+ *   (float), ab[nq][k][2] (uint16 A then B; optional).  Row i is sorted by
+ *   ascending (delta, idx).  When fewer than k descriptors exist, the extra
+ *   slots hold idx = 0xFFFFFFFF, score = +inf, A = B = 0xFFFF.
+ * Memory: every pointer named d_* is CUDA device memory owned by the caller
+ *   and must stay valid until the stream reaches the call's end.  The
+ *   library owns dt_index objects and any scratch space it allocates.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *   enqueue their work and return; outputs are ready when the stream is.
+ *   dt_build and calls that return host statistics synchronise the stream.
+ * Errors: every call returns DT_OK (0) or a negative status; on error no
+ *   output is guaranteed.  dt_status_string() names a status, and
+ *   dt_last_error() gives a message for the most recent failure in the
+ *   calling thread.
+ * Limits: 1 <= k <= DT_MAX_K; database size n <= DT_MAX_N; nq < 2^31.
+ */
+#ifndef DT_H
+#define DT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DT_WORDS 64
+#define DT_BITS 4096
+#define DT_MAX_K 32
+#define DT_MAX_N 2147483647LL
+
+enum {
+    DT_OK = 0,
+    DT_EINVAL = -1,        /* bad argument: null pointer, size, alignment, k */
+    DT_ENOMEM = -2,        /* device allocation failed */
+    DT_ECUDA = -3,         /* a CUDA runtime call failed */
+    DT_ETIMEOUT = -4,      /* a bounded device wait gave up */
+    DT_EUNSUPPORTED = -5   /* valid request this build/device cannot serve */
+};
+
+/* Opaque Dissimilarity Tree index; created by dt_build, freed by dt_free. */
+typedef struct dt_index dt_index;
+
+typedef struct {
+    int32_t leaf_size;      /* a node with at most this many descriptors is a leaf
+                               (§4.1; the paper found 32 best); <= 0 means 32 */
+    int32_t use_and_image;  /* nonzero: also keep each node's AND (product) image
+                               and add its type B term to the bound (§4) */
+    int32_t fused_cap;      /* nodes of at most this many descriptors are split by
+                               one thread block; larger ones by the multi-block
+                               path.  <= 0 means the default (2048).  Both paths
+                               compute the same split; this only tunes speed. */
+    int32_t reserved;       /* must be 0 */
+} dt_build_params;
+
+typedef struct {
+    int64_t n_nodes;        /* nodes, numbered breadth first */
+    int64_t n_leaves;
+    int32_t depth;          /* deepest level (root = 0) */
+    int32_t leaf_size;
+    int64_t n;              /* indexed descriptors */
+    int32_t use_and_image;
+    int32_t reserved;
+} dt_index_info;
+
+typedef struct {
+    int64_t nodes_visited;     /* nodes whose subtree was entered (inner + leaf) */
+    int64_t leaves_visited;    /* leaves scanned */
+    int64_t descs_scanned;     /* descriptors whose exact distance was computed */
+    int64_t bounds_evaluated;  /* node images read to bound a subtree */
+} dt_stats;
+
+/*
+ * dt_build — Dissimilarity Tree over n descriptors (§4.1).
+ *
+ * Each node with more than leaf_size descriptors is split in two.  Bit
+ * popularity = how many of the node's descriptors set each bit; bits are
+ * taken in ascending popularity (ties: lower bit index first) and every
+ * descriptor still in the similar set that has the current bit set moves to
+ * the dissimilar set, stopping right after the bit at which the dissimilar
+ * set first holds ceil(n/2) descriptors.  If a side would be empty, the
+ * node's descriptors (ascending index) are cut at floor(n/2) instead.  Every
+ * node stores the OR (sum) image of its descriptors.  Nodes are numbered
+ * breadth first, similar child before dissimilar child.
+ *
+ * d_db: [n][64] uint64 device array (n >= 1), read during the call only: the
+ *   index keeps its own tree-ordered copy.  params: nullable (defaults).
+ * out: receives the new index.  Synchronises `stream`.
+ * Errors: DT_EINVAL (null d_db/out, n < 1, n > DT_MAX_N, misaligned,
+ * reserved != 0), DT_ENOMEM, DT_ECUDA.
+ */
+int dt_build(const uint64_t *d_db, int64_t n, const dt_build_params *params, void *stream,
+             dt_index **out);
+
+/* Shape of a built index (host call, no device work). */
+int dt_get_info(const dt_index *index, dt_index_info *info);
+
+/*
+ * dt_export — copy the flattened tree to host memory (synchronous), for
+ * inspection and tests.  Any pointer may be NULL to skip that array.
+ *   h_child[n_nodes][2] int64: similar, dissimilar child; -1 at a leaf
+ *   h_begin[n_nodes], h_count[n_nodes] int64: the node's segment of h_perm
+ *   h_level[n_nodes] int32: depth
+ *   h_or[n_nodes][64], h_and[n_nodes][64] uint64: images (h_and requires an
+ *     index built with use_and_image)
+ *   h_perm[n] int64: tree position -> original database index
+ */
+int dt_export(const dt_index *index, int64_t *h_child, int64_t *h_begin, int64_t *h_count,
+              int32_t *h_level, uint64_t *h_or, uint64_t *h_and, int64_t *h_perm);
+
+/*
+ * dt_search — exact k nearest database descriptors of each query by
+ * Dissimilarity Tree traversal (§4.2).  A subtree is skipped only when its
+ * bound, popc(q & ~OR) * Z (+ popc(~q & AND) * P with AND images), is
+ * strictly greater than the current k-th result's A*Z + B*P, so the result
+ * equals bf_search's, ties included.
+ *
+ * d_q: [nq][64] queries.  d_idx, d_score: [nq][k].  d_ab: [nq][k][2] or NULL.
+ * h_stats: NULL, or host struct receiving totals over all queries (this
+ * synchronises the stream).  nq = 0 is a no-op.
+ * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_ETIMEOUT.
+ */
+int dt_search(const dt_index *index, const uint64_t *d_q, int64_t nq, int32_t k,
+              uint32_t *d_idx, float *d_score, uint16_t *d_ab, dt_stats *h_stats,
+              void *stream);
+
+/*
+ * bf_search — exact k nearest database descriptors by scanning all of them
+ * (the sequential search of §6.2).
+ *
+ * d_db: [n][64] database (n >= 1), d_q: [nq][64] queries; outputs as in
+ * dt_search.  path: 0 = automatic, 1 = popcount kernel, 2 = tensor-core
+ * kernel (DT_EUNSUPPORTED where not built).  Allocates scratch from the
+ * stream-ordered allocator.
+ * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_EUNSUPPORTED.
+ */
+int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,
+              uint32_t *d_idx, float *d_score, uint16_t *d_ab, int32_t path, void *stream);
+
+/*
+ * retrieve_objects — partial-object retrieval by voting (§3).
+ *
+ * Query j owns descriptors d_qdesc[d_qoffsets[j] .. d_qoffsets[j+1]).  Its
+ * descriptors are drawn in a random order (Fisher-Yates driven by SplitMix64,
+ * seeded from `seed` and j); each drawn descriptor's nearest database
+ * descriptor (top-1 by the tree) votes for its object d_object_of_desc[idx].
+ * With vote_threshold T > 0 drawing stops when an object reaches T votes and
+ * that object wins; with T = 0 every descriptor votes and the object with
+ * most votes wins (lowest id on ties).  A query without descriptors gets
+ * winner -1.
+ *
+ * d_object_of_desc: [n] uint32, indexed by original database index; ids
+ *   outside [0, n_objects) cast no vote.  d_qoffsets: [nq+1] int64 device array, non-decreasing,
+ *   d_qoffsets[0] = 0.  d_votes: [nq][n_objects] uint32 — the votes cast.
+ * d_winner: [nq] int32.  d_consumed: [nq] int64 descriptors drawn, or NULL.
+ * With T = 0 the call runs in one persistent launch and does not
+ * synchronise; with T > 0 it reads the descriptor total back (synchronises).
+ * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_ETIMEOUT.
+ */
+int retrieve_objects(const dt_index *index, const uint32_t *d_object_of_desc, int32_t n_objects,
+                     const uint64_t *d_qdesc, const int64_t *d_qoffsets, int32_t nq,
+                     int32_t vote_threshold, uint64_t seed, uint32_t *d_votes,
+                     int32_t *d_winner, int64_t *d_consumed, void *stream);
+
+/*
+ * dt_sync_status — wait for `stream`, then report a device-side failure
+ * raised by work enqueued since the previous dt_sync_status: DT_ETIMEOUT if
+ * a kernel gave up a bounded wait (its outputs are then incomplete), else
+ * DT_OK (or DT_ECUDA if the stream itself failed).  Clears the flags.
+ */
+int dt_sync_status(void *stream);
+
+/* Release an index (NULL is allowed).  Synchronises the device it lives on. */
+void dt_free(dt_index *index);
+
+/* Static name of a status code. */
+const char *dt_status_string(int status);
+
+/* Message for the last failing call in this thread ("" if none). */
+const char *dt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DT_H */

@@ -1,0 +1,233 @@
+// api.cu — the C ABI of include/dt.h: argument checks, index lifetime and
+// dispatch to the kernel launchers.  No computation happens here.
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dt_internal.cuh"
+
+namespace dtk {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (!cached[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+// A device (or managed) allocation; host pointers would make kernels fault.
+static bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace dtk
+
+using namespace dtk;
+
+#define REQUIRE_DEV(p, name)                                                     \
+    DT_CHECK_ARG((p) != nullptr && aligned16_ok(p) && is_device_ptr(p),           \
+                 std::string(name) + " must be a non-null device pointer")
+
+template <typename T>
+static bool aligned16_ok(const T *) { return true; }
+static bool aligned16_ok(const uint64_t *p) { return aligned16(p); }
+
+static int check_k(int32_t k)
+{
+    DT_CHECK_ARG(k >= 1 && k <= DT_MAX_K, "k must be in [1, DT_MAX_K]");
+    return DT_OK;
+}
+
+extern "C" {
+
+const char *dt_status_string(int status)
+{
+    switch (status) {
+    case DT_OK: return "DT_OK";
+    case DT_EINVAL: return "DT_EINVAL";
+    case DT_ENOMEM: return "DT_ENOMEM";
+    case DT_ECUDA: return "DT_ECUDA";
+    case DT_ETIMEOUT: return "DT_ETIMEOUT";
+    case DT_EUNSUPPORTED: return "DT_EUNSUPPORTED";
+    default: return "DT_UNKNOWN";
+    }
+}
+
+const char *dt_last_error(void) { return g_last_error.c_str(); }
+
+int dt_build(const uint64_t *d_db, int64_t n, const dt_build_params *params, void *stream,
+             dt_index **out)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(out != nullptr, "out must not be NULL");
+    *out = nullptr;
+    DT_CHECK_ARG(n >= 1 && n <= DT_MAX_N - 65536, "n out of range");
+    REQUIRE_DEV(d_db, "d_db");
+    dt_build_params p{32, 0, 0, 0};
+    if (params) p = *params;
+    DT_CHECK_ARG(p.reserved == 0, "params->reserved must be 0");
+    if (p.leaf_size <= 0) p.leaf_size = 32;
+    DT_CHECK_ARG(p.leaf_size <= 4096, "leaf_size must be <= 4096");
+    cudaStream_t s = (cudaStream_t)stream;
+    dt_index *ix = new dt_index();
+    DT_CUDA_TRY(cudaGetDevice(&ix->device));
+    int rc = build_tree(d_db, n, p.leaf_size, p.use_and_image ? 1 : 0, p.fused_cap, s, ix);
+    if (rc != DT_OK) {
+        dt_free(ix);
+        return rc;
+    }
+    *out = ix;
+    return DT_OK;
+}
+
+int dt_get_info(const dt_index *ix, dt_index_info *info)
+{
+    DT_CHECK_ARG(ix && info, "index and info must not be NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->n_nodes = ix->n_nodes;
+    info->n_leaves = ix->n_leaves;
+    info->depth = ix->depth;
+    info->leaf_size = ix->leaf_size;
+    info->n = ix->n;
+    info->use_and_image = ix->use_and;
+    return DT_OK;
+}
+
+int dt_export(const dt_index *ix, int64_t *h_child, int64_t *h_begin, int64_t *h_count,
+              int32_t *h_level, uint64_t *h_or, uint64_t *h_and, int64_t *h_perm)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
+    DT_CHECK_ARG(!h_and || ix->use_and, "index has no AND images");
+    const int64_t m = ix->n_nodes;
+    std::vector<NodeRec> recs((size_t)m);
+    DT_CUDA_TRY(cudaMemcpy(recs.data(), ix->node, (size_t)m * sizeof(NodeRec), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < m; ++i) {
+        const NodeRec &r = recs[(size_t)i];
+        if (h_child) {
+            h_child[2 * i] = r.first_child < 0 ? -1 : r.first_child;
+            h_child[2 * i + 1] = r.first_child < 0 ? -1 : r.first_child + 1;
+        }
+        if (h_begin) h_begin[i] = r.begin;
+        if (h_count) h_count[i] = r.count;
+        if (h_level) h_level[i] = r.level;
+    }
+    if (h_or)
+        DT_CUDA_TRY(cudaMemcpy(h_or, ix->or_img, (size_t)m * DT_WORDS * 8, cudaMemcpyDeviceToHost));
+    if (h_and)
+        DT_CUDA_TRY(cudaMemcpy(h_and, ix->and_img, (size_t)m * DT_WORDS * 8, cudaMemcpyDeviceToHost));
+    if (h_perm) {
+        std::vector<uint32_t> p((size_t)ix->n);
+        DT_CUDA_TRY(cudaMemcpy(p.data(), ix->perm, (size_t)ix->n * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < ix->n; ++i) h_perm[i] = p[(size_t)i];
+    }
+    return DT_OK;
+}
+
+int dt_search(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k, uint32_t *d_idx,
+              float *d_score, uint16_t *d_ab, dt_stats *h_stats, void *stream)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
+    if (int r = check_k(k)) return r;
+    DT_CHECK_ARG(nq >= 0 && nq < (1LL << 31), "nq out of range");
+    if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
+    if (nq == 0) return DT_OK;
+    REQUIRE_DEV(d_q, "d_q");
+    REQUIRE_DEV(d_idx, "d_idx");
+    REQUIRE_DEV(d_score, "d_score");
+    if (d_ab) REQUIRE_DEV(d_ab, "d_ab");
+    return launch_dt_search(ix, d_q, nq, k, d_idx, d_score, d_ab, h_stats, (cudaStream_t)stream);
+}
+
+int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,
+              uint32_t *d_idx, float *d_score, uint16_t *d_ab, int32_t path, void *stream)
+{
+    g_last_error.clear();
+    if (int r = check_k(k)) return r;
+    DT_CHECK_ARG(n >= 1 && n <= DT_MAX_N - 65536, "n out of range");
+    DT_CHECK_ARG(nq >= 0 && nq < (1LL << 31), "nq out of range");
+    DT_CHECK_ARG(path >= 0 && path <= 2, "path must be 0, 1 or 2");
+    if (nq == 0) return DT_OK;
+    REQUIRE_DEV(d_db, "d_db");
+    REQUIRE_DEV(d_q, "d_q");
+    REQUIRE_DEV(d_idx, "d_idx");
+    REQUIRE_DEV(d_score, "d_score");
+    if (d_ab) REQUIRE_DEV(d_ab, "d_ab");
+    if (path == 2) {
+        set_error("tensor-core path not available in this build");
+        return DT_EUNSUPPORTED;
+    }
+    return launch_bf_popc(d_db, n, d_q, nq, k, d_idx, d_score, d_ab, (cudaStream_t)stream);
+}
+
+int retrieve_objects(const dt_index *ix, const uint32_t *d_object_of_desc, int32_t n_objects,
+                     const uint64_t *d_qdesc, const int64_t *d_qoffsets, int32_t nq,
+                     int32_t vote_threshold, uint64_t seed, uint32_t *d_votes, int32_t *d_winner,
+                     int64_t *d_consumed, void *stream)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
+    DT_CHECK_ARG(n_objects >= 1, "n_objects must be >= 1");
+    DT_CHECK_ARG(nq >= 0, "nq must be >= 0");
+    DT_CHECK_ARG(vote_threshold >= 0, "vote_threshold must be >= 0");
+    if (nq == 0) return DT_OK;
+    REQUIRE_DEV(d_object_of_desc, "d_object_of_desc");
+    REQUIRE_DEV(d_qdesc, "d_qdesc");
+    REQUIRE_DEV(d_qoffsets, "d_qoffsets");
+    REQUIRE_DEV(d_votes, "d_votes");
+    REQUIRE_DEV(d_winner, "d_winner");
+    if (d_consumed) REQUIRE_DEV(d_consumed, "d_consumed");
+    return launch_retrieve(ix, d_object_of_desc, n_objects, d_qdesc, d_qoffsets, nq,
+                           vote_threshold, seed, d_votes, d_winner, d_consumed,
+                           (cudaStream_t)stream);
+}
+
+int dt_sync_status(void *stream)
+{
+    g_last_error.clear();
+    DT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    bool raised = false;
+    if (int r = take_bf_error(&raised)) return r;
+    if (raised) {
+        set_error("a database tile copy did not arrive within the spin limit");
+        return DT_ETIMEOUT;
+    }
+    return DT_OK;
+}
+
+void dt_free(dt_index *ix)
+{
+    if (!ix) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(ix->device);
+    cudaDeviceSynchronize();
+    cudaFree(ix->db_tree);
+    cudaFree(ix->perm);
+    cudaFree(ix->iperm);
+    cudaFree(ix->or_img);
+    cudaFree(ix->and_img);
+    cudaFree(ix->node);
+    cudaSetDevice(cur);
+    delete ix;
+}
+
+}  // extern "C"

@@ -1,0 +1,172 @@
+// dt_internal.cuh — shared pieces of the CUDA library behind include/dt.h.
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <cuda_runtime.h>
+
+#include "dt.h"
+
+namespace dtk {
+
+constexpr int kWords = DT_WORDS;      // uint64 words per descriptor
+constexpr int kBits = DT_BITS;
+constexpr int kMaxK = DT_MAX_K;
+constexpr uint64_t kEmpty = ~0ull;    // packed (key, idx) of a missing result
+
+// ---------------------------------------------------------------------------
+// Ranking key.  For a query with P = max(|q|,1), Z = max(4096-|q|,1), Eq. 1
+// times P*Z is the integer A*Z + B*P < 2^24, which orders targets exactly.
+// A result is packed as (key << 32) | idx so that one 64-bit comparison
+// ranks by (distance, index).
+// ---------------------------------------------------------------------------
+struct QueryWeights {
+    uint32_t pop, P, Z;
+};
+
+__host__ __device__ inline QueryWeights query_weights(uint32_t pop)
+{
+    QueryWeights w;
+    w.pop = pop;
+    w.P = pop > 1 ? pop : 1;
+    w.Z = (uint32_t)kBits - pop > 1 ? (uint32_t)kBits - pop : 1;
+    return w;
+}
+
+// A = |q| - O, B = |t| - O with O = popc(q & t).
+__device__ __forceinline__ uint32_t pair_key(const QueryWeights &w, uint32_t overlap,
+                                             uint32_t tpop)
+{
+    return (w.pop - overlap) * w.Z + (tpop - overlap) * w.P;
+}
+
+__device__ __forceinline__ uint64_t pack(uint32_t key, uint32_t idx)
+{
+    return ((uint64_t)key << 32) | idx;
+}
+
+// FP32 score: the exact rational key / (P*Z), correctly rounded (both
+// operands are exact in FP32: key < 2^24, P*Z <= 2^22).
+__device__ __forceinline__ float key_score(const QueryWeights &w, uint32_t key)
+{
+    return __fdiv_rn((float)key, (float)(w.P * w.Z));
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src)
+{
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u < v ? u : v;
+    }
+    return v;
+}
+
+// Sorted top-k list held across a warp: lane i holds the i-th smallest
+// packed result (kEmpty past the end).  Inserting v keeps the k smallest.
+__device__ __forceinline__ void warp_list_insert(uint64_t &slot, uint64_t v, int lane)
+{
+    uint64_t up = __shfl_up_sync(0xffffffffu, slot, 1);
+    if (lane == 0) up = 0;                 // nothing is smaller than lane 0's predecessor
+    if (slot > v) slot = (up > v) ? up : v;
+}
+
+// Merge the (lane-distributed, unsorted) candidates cand into the sorted
+// list; only candidates below the current k-th entry are inserted.
+__device__ __forceinline__ void warp_list_merge(uint64_t &slot, uint64_t cand, int k, int lane)
+{
+    uint64_t worst = shfl_u64(slot, k - 1);
+    unsigned m = __ballot_sync(0xffffffffu, cand < worst);
+    while (m) {
+        int src = __ffs(m) - 1;
+        m &= m - 1;
+        uint64_t v = shfl_u64(cand, src);
+        worst = shfl_u64(slot, k - 1);
+        if (v < worst) warp_list_insert(slot, v, lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+
+#define DT_CUDA_TRY(expr)                                                          \
+    do {                                                                           \
+        cudaError_t e_ = (expr);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            ::dtk::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));  \
+            return e_ == cudaErrorMemoryAllocation ? DT_ENOMEM : DT_ECUDA;         \
+        }                                                                          \
+    } while (0)
+
+#define DT_CHECK_ARG(cond, msg)                                                    \
+    do {                                                                           \
+        if (!(cond)) {                                                             \
+            ::dtk::set_error(msg);                                                 \
+            return DT_EINVAL;                                                      \
+        }                                                                          \
+    } while (0)
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int sm_count();
+
+// ---------------------------------------------------------------------------
+// Index
+// ---------------------------------------------------------------------------
+struct NodeRec {          // 16 bytes, one load per node
+    int32_t first_child;  // similar child id (dissimilar = +1); -1 at a leaf
+    int32_t begin;        // segment of the tree-ordered arrays
+    int32_t count;
+    int32_t level;
+};
+
+}  // namespace dtk
+
+struct dt_index {
+    int64_t n = 0;
+    int64_t n_nodes = 0;
+    int64_t n_leaves = 0;
+    int32_t depth = 0;
+    int32_t leaf_size = 32;
+    int32_t use_and = 0;
+    int device = 0;
+    uint64_t *db_tree = nullptr;    // [n][64] descriptors in tree order
+    uint32_t *perm = nullptr;       // [n] tree position -> original index
+    uint32_t *iperm = nullptr;      // [n] original index -> tree position
+    uint64_t *or_img = nullptr;     // [n_nodes][64]
+    uint64_t *and_img = nullptr;    // [n_nodes][64] when use_and
+    dtk::NodeRec *node = nullptr;   // [n_nodes]
+};
+
+namespace dtk {
+// Launchers implemented in the kernel files (stream-ordered, no sync unless noted).
+int take_bf_error(bool *raised);   // read and clear the brute-force timeout flag
+int launch_bf_popc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                   uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s);
+int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fused_cap,
+               cudaStream_t s, dt_index *ix);
+int launch_dt_search(const dt_index *ix, const uint64_t *q, int64_t nq, int k, uint32_t *idx,
+                     float *score, uint16_t *ab, dt_stats *stats, cudaStream_t s);
+int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects,
+                    const uint64_t *qdesc, const int64_t *qoffsets, int nq, int threshold,
+                    uint64_t seed, uint32_t *votes, int32_t *winner, int64_t *consumed,
+                    cudaStream_t s);
+}  // namespace dtk

@@ -1,0 +1,224 @@
+"""Python binding of libdt.so (include/dt.h): argument marshalling only.
+
+Every function here converts torch tensors to raw pointers, calls the C
+entry point of the same name and raises on a non-zero status.  All work runs
+in the library's CUDA kernels; there is no CPU fallback — if libdt.so cannot
+be built or loaded, importing this module fails.
+
+Tensor conventions (torch has no unsigned 64/32/16-bit arithmetic, so the
+unsigned C arrays are carried in signed tensors of the same width):
+  descriptors  int64 [n, 64] CUDA tensor holding the uint64 words
+  idx          int32 [nq, k]  (uint32 in C; 0xFFFFFFFF reads as -1)
+  score        float32 [nq, k]
+  ab           int16 [nq, k, 2]  (uint16 A, B)
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _build
+
+_lib = None
+
+DT_OK, DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_ETIMEOUT, DT_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+DT_MAX_K = 32
+WORDS = 64
+
+
+class DtError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        lib = load()
+        name = lib.dt_status_string(status).decode()
+        msg = lib.dt_last_error().decode()
+        super().__init__("%s failed: %s (%s)" % (where, name, msg))
+
+
+class BuildParams(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("use_and_image", ctypes.c_int32),
+                ("fused_cap", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class IndexInfo(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("use_and_image", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("nodes_visited", ctypes.c_int64), ("leaves_visited", ctypes.c_int64),
+                ("descs_scanned", ctypes.c_int64), ("bounds_evaluated", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def load():
+    """Build (if stale) and load libdt.so; raises if that is impossible."""
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_build.build_dt())
+        P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+        sig = {
+            "dt_build": ([P, i64, P, P, P], ctypes.c_int),
+            "dt_get_info": ([P, P], ctypes.c_int),
+            "dt_export": ([P, P, P, P, P, P, P, P], ctypes.c_int),
+            "dt_search": ([P, P, i64, i32, P, P, P, P, P], ctypes.c_int),
+            "bf_search": ([P, i64, P, i64, i32, P, P, P, i32, P], ctypes.c_int),
+            "retrieve_objects": ([P, P, i32, P, P, i32, i32, u64, P, P, P, P], ctypes.c_int),
+            "dt_sync_status": ([P], ctypes.c_int),
+            "dt_free": ([P], None),
+            "dt_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "dt_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+def _check(status, where):
+    if status != DT_OK:
+        raise DtError(status, where)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _desc(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int64
+            and t.dim() == 2 and t.shape[1] == WORDS and t.is_contiguous()):
+        raise ValueError("%s must be a contiguous CUDA int64 tensor of shape [n, 64]" % name)
+    return t
+
+
+class Index:
+    """Owns a dt_index*; freed by free() or when garbage-collected."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("index has been freed")
+        return self._h
+
+    def info(self):
+        inf = IndexInfo()
+        _check(load().dt_get_info(self.handle, ctypes.byref(inf)), "dt_get_info")
+        return {f: getattr(inf, f) for f, _ in IndexInfo._fields_ if f != "reserved"}
+
+    def export(self, with_and=False):
+        """Flattened tree as numpy arrays (child, begin, count, level, or_img, and_img, perm)."""
+        import numpy as np
+        inf = self.info()
+        m, n = inf["n_nodes"], inf["n"]
+        child = np.empty((m, 2), np.int64)
+        begin = np.empty(m, np.int64)
+        count = np.empty(m, np.int64)
+        level = np.empty(m, np.int32)
+        or_img = np.empty((m, WORDS), np.uint64)
+        and_img = np.empty((m, WORDS), np.uint64) if with_and else None
+        perm = np.empty(n, np.int64)
+        p = lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data)
+        _check(load().dt_export(self.handle, p(child), p(begin), p(count), p(level), p(or_img),
+                                p(and_img), p(perm)), "dt_export")
+        return dict(child=child, begin=begin, count=count, level=level, or_img=or_img,
+                    and_img=and_img, perm=perm)
+
+    def free(self):
+        if self._h is not None:
+            load().dt_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def dt_build(db, leaf_size=32, use_and_image=False, fused_cap=0, stream=None) -> Index:
+    db = _desc(db, "db")
+    params = BuildParams(leaf_size, 1 if use_and_image else 0, fused_cap, 0)
+    out = ctypes.c_void_p()
+    _check(load().dt_build(_ptr(db), db.shape[0], ctypes.byref(params), _stream(stream),
+                           ctypes.byref(out)), "dt_build")
+    return Index(out)
+
+
+def _outputs(nq, k, device, with_ab, out):
+    if out is not None:
+        return out
+    idx = torch.empty((nq, k), dtype=torch.int32, device=device)
+    score = torch.empty((nq, k), dtype=torch.float32, device=device)
+    ab = torch.empty((nq, k, 2), dtype=torch.int16, device=device) if with_ab else None
+    return idx, score, ab
+
+
+def dt_search(index: Index, q, k, with_ab=False, stats=False, out=None, stream=None):
+    """Returns (idx, score, ab or None, stats dict or None)."""
+    q = _desc(q, "q")
+    idx, score, ab = _outputs(q.shape[0], k, q.device, with_ab, out)
+    st = Stats() if stats else None
+    _check(load().dt_search(index.handle, _ptr(q), q.shape[0], k, _ptr(idx), _ptr(score),
+                            _ptr(ab), ctypes.byref(st) if st is not None else None,
+                            _stream(stream)), "dt_search")
+    return idx, score, ab, (st.as_dict() if st is not None else None)
+
+
+def bf_search(db, q, k, with_ab=False, path=0, out=None, stream=None):
+    """Returns (idx, score, ab or None)."""
+    db, q = _desc(db, "db"), _desc(q, "q")
+    idx, score, ab = _outputs(q.shape[0], k, q.device, with_ab, out)
+    _check(load().bf_search(_ptr(db), db.shape[0], _ptr(q), q.shape[0], k, _ptr(idx),
+                            _ptr(score), _ptr(ab), path, _stream(stream)), "bf_search")
+    return idx, score, ab
+
+
+def retrieve_objects(index: Index, object_of, n_objects, qdesc, qoffsets, vote_threshold=0,
+                     seed=0, with_consumed=True, out=None, stream=None):
+    """Returns (votes int32 [nq, n_objects] (uint32 counts), winner int32 [nq],
+    consumed int64 [nq] or None)."""
+    qdesc = _desc(qdesc, "qdesc")
+    if not (object_of.is_cuda and object_of.dtype == torch.int32 and object_of.is_contiguous()):
+        raise ValueError("object_of must be a contiguous CUDA int32 tensor")
+    if not (qoffsets.is_cuda and qoffsets.dtype == torch.int64 and qoffsets.is_contiguous()):
+        raise ValueError("qoffsets must be a contiguous CUDA int64 tensor")
+    nq = qoffsets.shape[0] - 1
+    dev = qdesc.device
+    if out is None:
+        votes = torch.empty((nq, n_objects), dtype=torch.int32, device=dev)
+        winner = torch.empty(nq, dtype=torch.int32, device=dev)
+        consumed = torch.empty(nq, dtype=torch.int64, device=dev) if with_consumed else None
+    else:
+        votes, winner, consumed = out
+    _check(load().retrieve_objects(index.handle, _ptr(object_of), n_objects, _ptr(qdesc),
+                                   _ptr(qoffsets), nq, vote_threshold, ctypes.c_uint64(seed),
+                                   _ptr(votes), _ptr(winner), _ptr(consumed), _stream(stream)),
+           "retrieve_objects")
+    return votes, winner, consumed
+
+
+def dt_sync_status(stream=None):
+    _check(load().dt_sync_status(_stream(stream)), "dt_sync_status")
+
+
+def dt_status_string(status):
+    return load().dt_status_string(status).decode()
+
+
+def dt_last_error():
+    return load().dt_last_error().decode()
