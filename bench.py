@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark: weighted-Hamming nearest-neighbour queries/s at 10M descriptors.
+
+Workload (synthetic, seeded): 10,000,000 QUICCI-like descriptors (64x64 bits,
+512 B each; 10,000 objects x 1,000 descriptors drawn from 50 curve sets per
+object) and 10,000 queries made from database descriptors with 30% of their
+set bits cleared and 0.5% of all bits flipped.  One step = one Dissimilarity
+Tree search (dt_search) of the whole 10,000-query batch for the top-10 by
+Eq. 1, against a tree built once beforehand; the GPU brute force (bf_search)
+over the same batch is timed beside it for the tree-vs-brute-force ratio.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (a bounded sample of queries per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "weighted-Hamming NN queries/s @10M descriptors: tree & learned vs GPU brute force"
+SEED = 210703368 + 1
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--n", type=int, default=10_000_000, help="database descriptors")
+    p.add_argument("--per-object", type=int, default=1000)
+    p.add_argument("--nq", type=int, default=10_000, help="queries per step")
+    p.add_argument("--k", type=int, default=10)
+    p.add_argument("--cpu-sample", type=int, default=32, help="queries the oracle times")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--bf-steps", type=int, default=1, help="timed brute-force passes")
+    return p.parse_args(argv)
+
+
+def workload_name(a):
+    return ("Dissimilarity Tree search, %d descriptors (%d objects x %d), %d queries, top-%d"
+            % (a.n, a.n // a.per_object, a.per_object, a.nq, a.k))
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; queries are sharded, no collective
+# on the data path: each rank searches its own batch against its own replica)
+# ---------------------------------------------------------------------------
+class Dist:
+    def __init__(self, backend):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group(backend=backend)
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def aggregate(per_rank_ms, units_per_rank, world):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (per_rank_ms / 1000.0)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_r%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_tree_leg(db, q, k, sample, nthreads):
+    """Build the oracle's tree (untimed), then time its best-first search on
+    `sample` queries.  Returns (queries/s, per-query best-first stats)."""
+    import oracle
+    tree = oracle.build(db, 32, nthreads=nthreads)
+    qs = q[:sample]
+    t0 = time.perf_counter()
+    _, _, _, st = oracle.tree_search(db, tree, qs, k, nthreads=nthreads)
+    dt_s = time.perf_counter() - t0
+    return sample / dt_s, st, tree
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+def run_reference(a, dist):
+    """The CPU oracle as the reference arm: best-first tree search of a
+    bounded sample of the same queries per step, on the host cores."""
+    if dist.rank != 0:
+        return 0
+    from paper_2107_03368_gb300 import synth
+    import oracle
+    db, _ = synth.database(SEED, a.n, per_object=a.per_object, nthreads=cpu_cores())
+    q, _ = synth.queries(SEED, db, max(a.nq, a.cpu_sample))
+    nt = cpu_cores()
+    tree = oracle.build(db, 32, nthreads=nt)
+    per_step = max(1, min(a.cpu_sample, a.nq))
+    times = []
+    for step in range(a.warmup + a.steps):
+        lo = (step * per_step) % max(1, q.shape[0] - per_step + 1)
+        t0 = time.perf_counter()
+        oracle.tree_search(db, tree, q[lo:lo + per_step], a.k, nthreads=nt)
+        if step >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    qps = per_step / (ms / 1000.0)
+    sample = ("%d queries per step (of the %d-query batch), best-first oracle tree search, "
+              "tree built untimed" % (per_step, a.nq))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(a), "n_db": a.n, "n_queries": a.nq, "k": a.k,
+                   "leaf_size": 32},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": nt, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(a, dist):
+    import torch
+    from paper_2107_03368_gb300 import dt, synth
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    stream = torch.cuda.current_stream(dev)
+    nt = cpu_cores()
+
+    db, _ = synth.database(SEED, a.n, per_object=a.per_object, nthreads=nt)
+    q_all, _ = synth.queries(SEED + 1000 * dist.rank, db, a.nq, nthreads=nt)
+    d_db = torch.from_numpy(db.view(np.int64)).to(dev)
+    d_q = torch.from_numpy(q_all.view(np.int64)).to(dev)
+    torch.cuda.synchronize()
+
+    t0 = time.perf_counter()
+    ix = dt.dt_build(d_db)
+    build_s = time.perf_counter() - t0
+    info = ix.info()
+
+    k = a.k
+    out = (torch.empty((a.nq, k), dtype=torch.int32, device=dev),
+           torch.empty((a.nq, k), dtype=torch.float32, device=dev), None)
+
+    def step():
+        dt.dt_search(ix, d_q, k, out=out)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dist.local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(a.steps):
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    dt.dt_sync_status()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = dist.max(sum(step_ms) / len(step_ms))
+    value = aggregate(ms, a.nq, dist.world)
+    tree_idx = out[0].clone()
+
+    # traversal statistics of the GPU search (one untimed run)
+    _, _, _, gst = dt.dt_search(ix, d_q, k, stats=True)
+
+    # end to end: pinned host queries in, results out, every step
+    h_q = torch.from_numpy(q_all.view(np.int64)).pin_memory()
+    h_idx = torch.empty((a.nq, k), dtype=torch.int32).pin_memory()
+    h_score = torch.empty((a.nq, k), dtype=torch.float32).pin_memory()
+    d_qe = torch.empty_like(d_q)
+    e_s = torch.cuda.Event(enable_timing=True)
+    e_e = torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e_s.record(stream)
+    for _ in range(a.steps):
+        d_qe.copy_(h_q, non_blocking=True)
+        idx_e, score_e, _, _ = dt.dt_search(ix, d_qe, k, out=out)
+        h_idx.copy_(idx_e, non_blocking=True)
+        h_score.copy_(score_e, non_blocking=True)
+    e_e.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = dist.max(e_s.elapsed_time(e_e) / a.steps)
+    e2e_value = aggregate(e2e_ms, a.nq, dist.world)
+
+    # GPU brute force on the same batch (the method's sequential search)
+    bf_out = (torch.empty((a.nq, k), dtype=torch.int32, device=dev),
+              torch.empty((a.nq, k), dtype=torch.float32, device=dev), None)
+    dt.bf_search(d_db, d_q, k, out=bf_out)          # warm
+    torch.cuda.synchronize()
+    b_s = torch.cuda.Event(enable_timing=True)
+    b_e = torch.cuda.Event(enable_timing=True)
+    b_s.record(stream)
+    for _ in range(a.bf_steps):
+        dt.bf_search(d_db, d_q, k, out=bf_out)
+    b_e.record(stream)
+    torch.cuda.synchronize()
+    bf_ms = b_s.elapsed_time(b_e) / a.bf_steps
+    bf_qps = a.nq / (bf_ms / 1000.0)
+    same = bool(torch.equal(bf_out[0], tree_idx))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": dist.world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "n_db": a.n, "n_queries": a.nq, "k": a.k,
+                   "leaf_size": 32, "tree_nodes": info["n_nodes"], "tree_depth": info["depth"],
+                   "l2": "inputs larger than L2 (%.2f GB database)" % (a.n * 512 / 1e9),
+                   "parallelism": "queries sharded, tree replicated" if dist.world > 1
+                   else "single GPU"},
+        "gpu_launches": a.steps,
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "queries/s",
+                "h2d_bytes_per_step": int(a.nq * 512),
+                "d2h_bytes_per_step": int(a.nq * k * 8)},
+        "bf_search": {"queries_per_s": bf_qps, "ms": bf_ms, "same_indices_as_tree": same},
+        "tree_vs_bf_speedup": value / dist.world / bf_qps,
+        "build_s": build_s,
+        "gpu_traversal_per_query": {kk: v / a.nq for kk, v in gst.items()},
+    }
+
+    # roofline of the dominant kernel (dt_search): algorithmic bytes per query =
+    # 512 B x (bounds evaluated + descriptors scanned) of the oracle's best-first
+    # search, measured on the cpu_baseline sample
+    peak, peak_kind = measured_peaks()
+    roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+            "traffic": None, "peak_kind": peak_kind}
+    if dist.rank == 0 and not a.no_cpu_baseline:
+        sample = min(a.cpu_sample, a.nq)
+        cpu_qps, ost, _ = oracle_tree_leg(db, q_all, k, sample, nt)
+        bytes_per_q = 512.0 * float(np.mean(ost[:, 3] + ost[:, 2]))
+        achieved = bytes_per_q * a.nq / (ms / 1000.0) / 1e9
+        roof.update(achieved=achieved, frac=achieved / peak,
+                    bytes_per_query=bytes_per_q, oracle_sample=sample)
+        line["cpu_baseline"] = {
+            "value": cpu_qps, "unit": "queries/s", "cores": nt, "kind": "oracle",
+            "sample": "%d of the %d queries, best-first oracle tree search (tree built untimed)"
+                      % (sample, a.nq)}
+        line["oracle_best_first_per_query"] = {
+            "nodes_popped": float(np.mean(ost[:, 0])), "leaves": float(np.mean(ost[:, 1])),
+            "descs_scanned": float(np.mean(ost[:, 2])), "bounds": float(np.mean(ost[:, 3]))}
+    line["roofline"] = roof
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    ix.free()
+    return 0
+
+
+def main(argv=None):
+    a = parse_args(argv)
+    if a.impl == "reference":
+        dist = Dist("gloo")
+        try:
+            return run_reference(a, dist)
+        finally:
+            dist.close()
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    dist = Dist("nccl")
+    try:
+        return run_ours(a, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

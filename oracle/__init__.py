@@ -61,7 +61,7 @@ def _load():
         lib.orc_wh.restype = f64
         lib.orc_bf_topk.argtypes = [P, i64, P, i64, i32, P, P, P, i32]
         lib.orc_bf_topk.restype = None
-        lib.orc_build.argtypes = [P, i64, i32, i32, P, P, P, P, P, P, P]
+        lib.orc_build.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P, P, P]
         lib.orc_build.restype = i64
         lib.orc_node_bound.argtypes = [P, P, P]
         lib.orc_node_bound.restype = i64
@@ -156,7 +156,7 @@ class Tree:
         return self.perm[b:b + c]
 
 
-def build(db, leaf_size=32, literal=False, with_and=False):
+def build(db, leaf_size=32, literal=False, with_and=False, nthreads=0):
     db = _desc(db)
     n = db.shape[0]
     cap = max(2 * n, 1)
@@ -167,7 +167,8 @@ def build(db, leaf_size=32, literal=False, with_and=False):
     or_img = np.empty((cap, WORDS), dtype=np.uint64)
     and_img = np.empty((cap, WORDS), dtype=np.uint64) if with_and else None
     perm = np.empty(max(n, 1), dtype=np.int64)
-    m = _load().orc_build(_p(db), n, leaf_size, 1 if literal else 0, _p(child), _p(begin),
+    m = _load().orc_build(_p(db), n, leaf_size, 1 if literal else 0, _threads(nthreads),
+                          _p(child), _p(begin),
                           _p(count), _p(level), _p(or_img), _p(and_img), _p(perm))
     return Tree(child[:m].copy(), begin[:m].copy(), count[:m].copy(), level[:m].copy(),
                 or_img[:m].copy(), None if and_img is None else and_img[:m].copy(),

@@ -304,9 +304,15 @@ static int cmp_u64(const void *x, const void *y)
  * descriptors if fewer than ceil(n/2) exist).  Counting only the set bits
  * makes it fast enough for millions of descriptors.
  */
+/* Large nodes (a level with fewer nodes than threads) also spread their
+ * per-descriptor loops over threads; both loops are independent per
+ * descriptor (the counts are summed, the minima written per descriptor). */
+#define ORC_PAR_MIN 200000
+
 static int64_t split_minrank(const uint64_t *db, int64_t *list, int64_t n)
 {
     int64_t *counts = (int64_t *)calloc(OBITS, sizeof(int64_t));
+#pragma omp parallel for reduction(+ : counts[:OBITS]) if (n >= ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         const uint64_t *d = db + list[i] * OW;
         for (int w = 0; w < OW; ++w) {
@@ -320,6 +326,7 @@ static int64_t split_minrank(const uint64_t *db, int64_t *list, int64_t n)
     const uint64_t NONE = UINT64_MAX;
     uint64_t *mk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
     uint64_t *sorted = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+#pragma omp parallel for if (n >= ORC_PAR_MIN)
     for (int64_t i = 0; i < n; ++i) {
         const uint64_t *d = db + list[i] * OW;
         uint64_t m = NONE;
@@ -377,42 +384,62 @@ static void node_images(const uint64_t *db, const int64_t *list, int64_t n,
 }
 
 /*
- * Builds the tree breadth first (a FIFO of pending nodes); the recursion of
- * the listing visits the same nodes with the same splits, only in another
- * order.  literal != 0 selects the bit-by-bit move loop, else the closed
- * form.  Returns the number of nodes.
+ * Builds the tree one level at a time (breadth first); the recursion of the
+ * listing visits the same nodes with the same splits, only in another
+ * order.  The nodes of a level own disjoint segments of perm, so they are
+ * split independently (OpenMP threads over a level's nodes); children are
+ * then numbered in level order, similar child first.  literal != 0 selects
+ * the bit-by-bit move loop, else the closed form.  Returns the node count.
  */
 int64_t orc_build(const uint64_t *db, int64_t n, int32_t leaf_size, int32_t literal,
-                  int64_t *child, int64_t *begin, int64_t *count, int32_t *level,
-                  uint64_t *or_img, uint64_t *and_img, int64_t *perm)
+                  int32_t nthreads, int64_t *child, int64_t *begin, int64_t *count,
+                  int32_t *level, uint64_t *or_img, uint64_t *and_img, int64_t *perm)
 {
     if (n <= 0) return 0;
     for (int64_t i = 0; i < n; ++i) perm[i] = i;
-    int64_t cap = 2 * n;
-    work_t *queue = (work_t *)malloc(sizeof(work_t) * (size_t)cap);
-    int64_t head = 0, tail = 0, next_id = 1;
-    queue[tail++] = (work_t){ 0, 0, n, 0 };
-    while (head < tail) {
-        work_t w = queue[head++];
-        int64_t *list = perm + w.begin;
-        begin[w.node] = w.begin;
-        count[w.node] = w.count;
-        level[w.node] = w.level;
-        node_images(db, list, w.count, or_img + w.node * OW,
-                    and_img ? and_img + w.node * OW : NULL);
-        if (w.count <= leaf_size) {            /* reading R5 */
-            child[2 * w.node] = child[2 * w.node + 1] = -1;
-            continue;
+    work_t *cur = (work_t *)malloc(sizeof(work_t) * (size_t)(n + 1));
+    work_t *next = (work_t *)malloc(sizeof(work_t) * (size_t)(n + 1));
+    int64_t *n_sim = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int64_t m = 1, next_id = 1;
+    cur[0] = (work_t){ 0, 0, n, 0 };
+    int nt = nthreads > 0 ? nthreads : 1;
+    while (m > 0) {
+        /* few nodes: one at a time, each using all threads inside */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt) if (m >= nt)
+        for (int64_t i = 0; i < m; ++i) {
+            work_t w = cur[i];
+            int64_t *list = perm + w.begin;
+            begin[w.node] = w.begin;
+            count[w.node] = w.count;
+            level[w.node] = w.level;
+            node_images(db, list, w.count, or_img + w.node * OW,
+                        and_img ? and_img + w.node * OW : NULL);
+            if (w.count <= leaf_size) {        /* reading R5 */
+                n_sim[i] = -1;
+                continue;
+            }
+            n_sim[i] = literal ? split_literal(db, list, w.count)
+                               : split_minrank(db, list, w.count);
         }
-        int64_t n_sim = literal ? split_literal(db, list, w.count)
-                                : split_minrank(db, list, w.count);
-        int64_t s = next_id++, d = next_id++;
-        child[2 * w.node] = s;
-        child[2 * w.node + 1] = d;
-        queue[tail++] = (work_t){ s, w.begin, n_sim, w.level + 1 };
-        queue[tail++] = (work_t){ d, w.begin + n_sim, w.count - n_sim, w.level + 1 };
+        int64_t m2 = 0;
+        for (int64_t i = 0; i < m; ++i) {
+            work_t w = cur[i];
+            if (n_sim[i] < 0) {
+                child[2 * w.node] = child[2 * w.node + 1] = -1;
+                continue;
+            }
+            int64_t s = next_id++, d = next_id++;
+            child[2 * w.node] = s;
+            child[2 * w.node + 1] = d;
+            next[m2++] = (work_t){ s, w.begin, n_sim[i], w.level + 1 };
+            next[m2++] = (work_t){ d, w.begin + n_sim[i], w.count - n_sim[i], w.level + 1 };
+        }
+        work_t *t = cur; cur = next; next = t;
+        m = m2;
     }
-    free(queue);
+    free(n_sim);
+    free(next);
+    free(cur);
     return next_id;
 }
 
