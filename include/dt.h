@@ -163,6 +163,35 @@ int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, 
               uint32_t *d_idx, float *d_score, uint16_t *d_ab, int32_t path, void *stream);
 
 /*
+ * bf_search_noalloc — bf_search (path 1, popcount kernel) that allocates no
+ * memory at all.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let a library allocate device memory, for example a
+ * serving process that has divided the GPU among models in advance or a host
+ * framework that owns all device memory through its own arena.  For them a
+ * hidden cudaMalloc / cudaMallocAsync can fail at an arbitrary moment, may
+ * synchronise the device, and escapes their memory accounting.
+ *
+ * The caller passes inputs and outputs exactly as for bf_search.  The only
+ * scratch (the per-split top-k lists) lives in a fixed array of
+ * DT_NOALLOC_SCRATCH_BYTES compiled into the library; every GPU that loads
+ * the library holds that array until the process exits.
+ *   Limit: nq * k * 8 <= DT_NOALLOC_SCRATCH_BYTES (nq * k <= 2,097,152);
+ *   larger requests return DT_EINVAL without touching the GPU — split the
+ *   queries into batches.
+ *   Set-up: the first call on a device (with that device current) looks up
+ *   the array's device address; make that first call before any stream
+ *   capture.
+ *   Sharing: all calls on a device share the array and it keeps the last
+ *   call's contents (nothing in it needs to start at zero).  Calls whose
+ *   work overlaps on the GPU (e.g. on two unordered streams) race on it;
+ *   order them on one stream.
+ * Results are identical to bf_search's.  Errors: DT_EINVAL, DT_ECUDA.
+ */
+#define DT_NOALLOC_SCRATCH_BYTES (16u << 20)
+int bf_search_noalloc(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,
+                      uint32_t *d_idx, float *d_score, uint16_t *d_ab, void *stream);
+
+/*
  * retrieve_objects — partial-object retrieval by voting (§3).
  *
  * Query j owns descriptors d_qdesc[d_qoffsets[j] .. d_qoffsets[j+1]).  Its

@@ -178,6 +178,27 @@ int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, 
     return launch_bf_popc(d_db, n, d_q, nq, k, d_idx, d_score, d_ab, (cudaStream_t)stream);
 }
 
+// Same checks as bf_search; the size limit of the fixed scratch is checked
+// before any CUDA call, and nothing here or below allocates.
+int bf_search_noalloc(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,
+                      uint32_t *d_idx, float *d_score, uint16_t *d_ab, void *stream)
+{
+    g_last_error.clear();
+    if (int r = check_k(k)) return r;
+    DT_CHECK_ARG(n >= 1 && n <= DT_MAX_N - 65536, "n out of range");
+    DT_CHECK_ARG(nq >= 0 && nq < (1LL << 31), "nq out of range");
+    DT_CHECK_ARG((uint64_t)nq * (uint64_t)k * 8u <= (uint64_t)DT_NOALLOC_SCRATCH_BYTES,
+                 "bf_search_noalloc: nq * k * 8 exceeds DT_NOALLOC_SCRATCH_BYTES; "
+                 "search the queries in smaller batches");
+    if (nq == 0) return DT_OK;
+    REQUIRE_DEV(d_db, "d_db");
+    REQUIRE_DEV(d_q, "d_q");
+    REQUIRE_DEV(d_idx, "d_idx");
+    REQUIRE_DEV(d_score, "d_score");
+    if (d_ab) REQUIRE_DEV(d_ab, "d_ab");
+    return launch_bf_popc_noalloc(d_db, n, d_q, nq, k, d_idx, d_score, d_ab, (cudaStream_t)stream);
+}
+
 int retrieve_objects(const dt_index *ix, const uint32_t *d_object_of_desc, int32_t n_objects,
                      const uint64_t *d_qdesc, const int64_t *d_qoffsets, int32_t nq,
                      int32_t vote_threshold, uint64_t seed, uint32_t *d_votes, int32_t *d_winner,

@@ -22,6 +22,7 @@
 //     kernel merges the per-split lists and writes idx / score / (A, B).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "dt_internal.cuh"
@@ -298,6 +299,92 @@ int launch_bf_popc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq,
                                                                            nq, k, idx, score, ab);
     DT_CUDA_TRY(cudaGetLastError());
     DT_CUDA_TRY(cudaFreeAsync(partial, s));
+    return DT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Brute force without any allocation (bf_search_noalloc).
+//
+// The only scratch the brute force needs is the per-split top-k lists that
+// the merge kernel combines.  Here they live in one fixed array compiled into
+// the library, so the call makes no cudaMalloc / cudaMallocAsync / cudaFree.
+// The array is shared by every call on a device and keeps the previous
+// call's contents; nothing in it has to start at zero, because every list
+// entry that the merge reads is written first by the same call.  Two calls
+// whose work overlaps on the GPU (different streams, no ordering between
+// them) use the same array and race.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) uint64_t g_noalloc_partial[DT_NOALLOC_SCRATCH_BYTES / 8];
+
+struct NoallocDevice {
+    bool ready = false;
+    uint64_t *partial = nullptr;   // device address of g_noalloc_partial
+    uint32_t *err = nullptr;       // device address of g_bf_error
+};
+
+std::mutex g_noalloc_mu;
+NoallocDevice g_noalloc_dev[64];
+
+// Per-device set-up on the current device: resolve the device addresses of
+// the static arrays (a host-side name of a __device__ array is not a device
+// address) and set the kernel's shared-memory limit.
+int noalloc_setup(NoallocDevice **out)
+{
+    int dev = 0;
+    DT_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        set_error("bf_search_noalloc: device ordinal out of range");
+        return DT_EUNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void *p = nullptr, *e = nullptr;
+        DT_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_partial));
+        DT_CUDA_TRY(cudaGetSymbolAddress(&e, g_bf_error));
+        DT_CUDA_TRY(cudaFuncSetAttribute(bf_popc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(BfSmem) + QB * kMaxK * sizeof(uint64_t))));
+        d.partial = static_cast<uint64_t *>(p);
+        d.err = static_cast<uint32_t *>(e);
+        d.ready = true;
+    }
+    *out = &d;
+    return DT_OK;
+}
+
+}  // namespace
+
+int launch_bf_popc_noalloc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                           uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s)
+{
+    const uint64_t list_bytes = (uint64_t)nq * (uint64_t)k * sizeof(uint64_t);
+    if (list_bytes > DT_NOALLOC_SCRATCH_BYTES) {
+        set_error("bf_search_noalloc: nq * k * 8 bytes exceeds the fixed scratch of "
+                  "DT_NOALLOC_SCRATCH_BYTES; split the queries into smaller batches");
+        return DT_EINVAL;
+    }
+    NoallocDevice *d = nullptr;
+    if (int r = noalloc_setup(&d)) return r;
+    const size_t smem = sizeof(BfSmem) + (size_t)QB * k * sizeof(uint64_t);
+    const int64_t qblocks = (nq + QB - 1) / QB;
+    const int64_t tiles = (n + TB - 1) / TB;
+    int per_sm = 0;
+    DT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf_popc_kernel, THREADS, smem));
+    const int concurrent = std::max(1, per_sm) * sm_count();
+    // as many database splits as the fixed scratch holds lists for
+    const int64_t fit = (int64_t)(DT_NOALLOC_SCRATCH_BYTES / list_bytes);
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(pick_splits(qblocks, tiles, concurrent), fit));
+    const int64_t tiles_per_split = (tiles + splits - 1) / splits;
+    const int n_split = (int)((tiles + tiles_per_split - 1) / tiles_per_split);
+    dim3 grid((unsigned)qblocks, (unsigned)n_split);
+    bf_popc_kernel<<<grid, THREADS, smem, s>>>(db, n, q, nq, k, tiles_per_split, d->partial, d->err);
+    DT_CUDA_TRY(cudaGetLastError());
+    const int wpb = 8;
+    bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(d->partial, n_split, db, q,
+                                                                           nq, k, idx, score, ab);
+    DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
 

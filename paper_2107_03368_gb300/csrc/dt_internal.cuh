@@ -159,6 +159,8 @@ struct dt_index {
 namespace dtk {
 // Launchers implemented in the kernel files (stream-ordered, no sync unless noted).
 int take_bf_error(bool *raised);   // read and clear the brute-force timeout flag
+int launch_bf_popc_noalloc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                           uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s);
 int launch_bf_popc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                    uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s);
 int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fused_cap,

@@ -68,6 +68,7 @@ def load():
             "dt_export": ([P, P, P, P, P, P, P, P], ctypes.c_int),
             "dt_search": ([P, P, i64, i32, P, P, P, P, P], ctypes.c_int),
             "bf_search": ([P, i64, P, i64, i32, P, P, P, i32, P], ctypes.c_int),
+            "bf_search_noalloc": ([P, i64, P, i64, i32, P, P, P, P], ctypes.c_int),
             "retrieve_objects": ([P, P, i32, P, P, i32, i32, u64, P, P, P, P], ctypes.c_int),
             "dt_sync_status": ([P], ctypes.c_int),
             "dt_free": ([P], None),
@@ -185,6 +186,18 @@ def bf_search(db, q, k, with_ab=False, path=0, out=None, stream=None):
     idx, score, ab = _outputs(q.shape[0], k, q.device, with_ab, out)
     _check(load().bf_search(_ptr(db), db.shape[0], _ptr(q), q.shape[0], k, _ptr(idx),
                             _ptr(score), _ptr(ab), path, _stream(stream)), "bf_search")
+    return idx, score, ab
+
+
+def bf_search_noalloc(db, q, k, out, stream=None):
+    """bf_search that allocates nothing, neither in the library nor here: the
+    caller provides out = (idx, score, ab or None).  For callers that must
+    not have device memory allocated behind their back (a fixed per-process
+    memory plan, an external arena); limit nq * k <= 2,097,152."""
+    db, q = _desc(db, "db"), _desc(q, "q")
+    idx, score, ab = out
+    _check(load().bf_search_noalloc(_ptr(db), db.shape[0], _ptr(q), q.shape[0], k, _ptr(idx),
+                                    _ptr(score), _ptr(ab), _stream(stream)), "bf_search_noalloc")
     return idx, score, ab
 
 
