@@ -24,6 +24,7 @@ OBJ_DIR = os.path.join(HERE, "_build")
 CUDA_SOURCES = [
     "api.cu",
     "bf_popc.cu",
+    "bf_tc.cu",
     "dt_build.cu",
     "dt_search.cu",
     "votes.cu",

@@ -171,10 +171,8 @@ int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, 
     REQUIRE_DEV(d_idx, "d_idx");
     REQUIRE_DEV(d_score, "d_score");
     if (d_ab) REQUIRE_DEV(d_ab, "d_ab");
-    if (path == 2) {
-        set_error("tensor-core path not available in this build");
-        return DT_EUNSUPPORTED;
-    }
+    if (path == 2)
+        return launch_bf_tc(d_db, n, d_q, nq, k, d_idx, d_score, d_ab, (cudaStream_t)stream);
     return launch_bf_popc(d_db, n, d_q, nq, k, d_idx, d_score, d_ab, (cudaStream_t)stream);
 }
 
@@ -225,8 +223,10 @@ int dt_sync_status(void *stream)
 {
     g_last_error.clear();
     DT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    bool raised = false;
+    bool raised = false, raised_tc = false;
     if (int r = take_bf_error(&raised)) return r;
+    if (int r = take_tc_error(&raised_tc)) return r;
+    raised = raised || raised_tc;
     if (raised) {
         set_error("a database tile copy did not arrive within the spin limit");
         return DT_ETIMEOUT;

@@ -259,6 +259,22 @@ int pick_splits(int64_t qblocks, int64_t tiles, int concurrent)
 
 }  // namespace
 
+int pick_bf_splits(int64_t row_blocks, int64_t tiles, int concurrent)
+{
+    return pick_splits(row_blocks, tiles, concurrent);
+}
+
+int launch_merge_partials(const uint64_t *partial, int n_split, const uint64_t *db,
+                          const uint64_t *q, int64_t nq, int k, uint32_t *idx, float *score,
+                          uint16_t *ab, cudaStream_t s)
+{
+    const int wpb = 8;
+    bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(partial, n_split, db, q,
+                                                                           nq, k, idx, score, ab);
+    DT_CUDA_TRY(cudaGetLastError());
+    return DT_OK;
+}
+
 int take_bf_error(bool *raised)
 {
     uint32_t v = 0, zero = 0;

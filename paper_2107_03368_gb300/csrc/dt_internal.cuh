@@ -158,6 +158,14 @@ struct dt_index {
 
 namespace dtk {
 // Launchers implemented in the kernel files (stream-ordered, no sync unless noted).
+int pick_bf_splits(int64_t row_blocks, int64_t tiles, int concurrent);
+// Merge per-split sorted top-k lists partial[split][q][k] into idx/score/(A,B).
+int launch_merge_partials(const uint64_t *partial, int n_split, const uint64_t *db,
+                          const uint64_t *q, int64_t nq, int k, uint32_t *idx, float *score,
+                          uint16_t *ab, cudaStream_t s);
+int launch_bf_tc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                 uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s);
+int take_tc_error(bool *raised);
 int take_bf_error(bool *raised);   // read and clear the brute-force timeout flag
 int launch_bf_popc_noalloc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                            uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s);

@@ -147,8 +147,25 @@ void synth_db(uint64_t seed, int64_t n, int64_t per_object, int32_t pool,
     }
 }
 
+/* Number of flips among 4096 independent Bernoulli(p) bits, by inversion of
+ * the Binomial(4096, p) distribution (pmf by the ratio recurrence). */
+static int binomial_4096(double p, uint64_t *s)
+{
+    double u = unif(s), q = 1.0 - p, pmf = 1.0;
+    for (int i = 0; i < 4096; ++i) pmf *= q;          /* P(K = 0) */
+    double cdf = pmf;
+    int k = 0;
+    while (u >= cdf && k < 4096) {
+        pmf *= (double)(4096 - k) / (double)(k + 1) * (p / q);
+        cdf += pmf;
+        ++k;
+    }
+    return k;
+}
+
 /* Clear each set bit with probability p_clear, then flip every bit with
- * probability p_flip (stream s). */
+ * probability p_flip (stream s): a Binomial(4096, p_flip) count of distinct
+ * positions, drawn uniformly, which is the same distribution. */
 static void add_noise(uint64_t *d, double p_clear, double p_flip, uint64_t *s)
 {
     for (int w = 0; w < SY_WORDS; ++w) {
@@ -159,9 +176,17 @@ static void add_noise(uint64_t *d, double p_clear, double p_flip, uint64_t *s)
             if (unif(s) < p_clear) d[w] &= ~(1ULL << b);
         }
     }
-    for (int w = 0; w < SY_WORDS; ++w)
-        for (int b = 0; b < 64; ++b)
-            if (unif(s) < p_flip) d[w] ^= 1ULL << b;
+    if (p_flip <= 0.0) return;
+    int k = binomial_4096(p_flip, s);
+    uint64_t flip[SY_WORDS] = {0};
+    for (int done = 0; done < k;) {
+        int pos = (int)(sm_next(s) >> 52);             /* 12 random bits */
+        uint64_t m = 1ULL << (pos & 63);
+        if (flip[pos >> 6] & m) continue;               /* distinct positions */
+        flip[pos >> 6] |= m;
+        ++done;
+    }
+    for (int w = 0; w < SY_WORDS; ++w) d[w] ^= flip[w];
 }
 
 /* nq queries: a uniformly drawn database descriptor, partiality + noise.

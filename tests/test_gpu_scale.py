@@ -1,0 +1,111 @@
+"""Full-size parity on the GPU.
+
+- Tree search at scale (10,000,000 descriptors, 10,000 queries, top-10, the
+  benchmark's configuration): dt_search equals bf_search for every query
+  (indices, (A, B) counts, scores), and a spread sample of queries equals the
+  oracle's exact top-10; sampled tree nodes satisfy the structural facts.
+- Partial-object retrieval on the 400-object x 25,000-descriptor database:
+  votes equal the histogram of the brute-force nearest neighbours' objects
+  (a separate GPU path) for a subset of uneven partial queries, and sampled
+  nearest neighbours equal the oracle's.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import SCORE_RTOL, idx_np, to_dev, u16_np
+from paper_2107_03368_gb300 import dt, synth
+
+pytestmark = pytest.mark.gpu
+
+SEED = 210703368 + 1
+
+
+@pytest.fixture(scope="module")
+def big():
+    db, _ = synth.database(SEED, 10_000_000, per_object=1000)
+    q, _ = synth.queries(SEED, db, 10_000)
+    d_db, d_q = to_dev(db), to_dev(q)
+    ix = dt.dt_build(d_db)
+    yield db, q, d_db, d_q, ix
+    ix.free()
+
+
+def test_tree_equals_brute_force_all_queries(big):
+    db, q, d_db, d_q, ix = big
+    t_idx, t_score, t_ab, _ = dt.dt_search(ix, d_q, 10, with_ab=True)
+    b_idx, b_score, b_ab = dt.bf_search(d_db, d_q, 10, with_ab=True, path=1)
+    c_idx, c_score, c_ab = dt.bf_search(d_db, d_q, 10, with_ab=True, path=2)
+    dt.dt_sync_status()
+    for idx, score, ab in ((b_idx, b_score, b_ab), (c_idx, c_score, c_ab)):
+        assert torch.equal(t_idx, idx)
+        assert torch.equal(t_ab, ab)
+        assert torch.equal(t_score, score)
+
+
+def test_sampled_queries_equal_oracle(big):
+    db, q, d_db, d_q, ix = big
+    pick = np.linspace(0, q.shape[0] - 1, 12).astype(np.int64)
+    t_idx, t_score, t_ab, _ = dt.dt_search(ix, d_q, 10, with_ab=True)
+    o_idx, o_score, o_ab = oracle.bf_topk(db, q[pick], 10)
+    assert np.array_equal(idx_np(t_idx)[pick], o_idx)
+    assert np.array_equal(u16_np(t_ab)[pick], o_ab)
+    np.testing.assert_allclose(t_score.cpu().numpy()[pick], o_score, rtol=SCORE_RTOL, atol=0)
+
+
+def test_sampled_nodes_structure(big):
+    db, q, d_db, d_q, ix = big
+    t = ix.export()
+    m = t["count"].shape[0]
+    assert t["count"][0] == db.shape[0]
+    assert sorted(t["perm"][:1000].tolist()) == sorted(set(t["perm"][:1000].tolist()))
+    rng = np.random.default_rng(0)
+    for node in rng.integers(0, m, size=200):
+        b, c = t["begin"][node], t["count"][node]
+        mem = t["perm"][b:b + c]
+        assert np.array_equal(np.bitwise_or.reduce(db[mem], axis=0), t["or_img"][node])
+        s, d = t["child"][node]
+        if s < 0:
+            assert c <= 32 and np.all(np.diff(mem) > 0)
+        else:
+            assert c > 32
+            assert t["begin"][s] == b and t["begin"][d] == b + t["count"][s]
+            assert t["count"][s] + t["count"][d] == c and t["count"][s] > 0
+
+
+def test_partial_retrieval_on_full_database():
+    n_obj, per = 400, 25_000
+    db, obj = synth.database(SEED + 2, n_obj * per, per_object=per)
+    qd, off, qobj = synth.partial_queries(SEED + 2, db, n_obj, per, 1000)
+    sub = 4                                            # first 4 uneven queries
+    off_s = off[: sub + 1].copy()
+    qd_s = qd[: off_s[-1]]
+    sizes = np.diff(off_s)
+    assert sizes.min() >= 500 and sizes.max() <= 10_000
+    d_db = to_dev(db)
+    ix = dt.dt_build(d_db)
+    d_obj = torch.from_numpy(obj.view(np.int32)).cuda()
+    d_qd = to_dev(qd_s)
+    votes, winner, consumed = dt.retrieve_objects(ix, d_obj, n_obj, d_qd,
+                                                  torch.from_numpy(off_s).cuda(), 0, SEED)
+    b_idx, _, _ = dt.bf_search(d_db, d_qd, 1)
+    nn = idx_np(b_idx)[:, 0]
+    v = votes.cpu().numpy().view(np.uint32)
+    for j in range(sub):
+        hist = np.bincount(obj[nn[off_s[j]:off_s[j + 1]]], minlength=n_obj)
+        assert np.array_equal(v[j], hist)
+        assert winner[j].item() == int(np.argmax(hist))
+    assert np.array_equal(consumed.cpu().numpy(), sizes)
+    assert np.all(winner.cpu().numpy() == qobj[:sub])
+    pick = np.linspace(0, qd_s.shape[0] - 1, 8).astype(np.int64)
+    o_idx, _, _ = oracle.bf_topk(db, qd_s[pick], 1)
+    assert np.array_equal(nn[pick], o_idx[:, 0])
+    # threshold 10: the winner reaches exactly 10 votes within the draws
+    votes10, winner10, used10 = dt.retrieve_objects(ix, d_obj, n_obj, d_qd,
+                                                    torch.from_numpy(off_s).cuda(), 10, SEED)
+    v10 = votes10.cpu().numpy().view(np.uint32)
+    for j in range(sub):
+        w = winner10[j].item()
+        assert v10[j, w] == 10 and v10[j].sum() == used10[j].item() <= sizes[j]
+    ix.free()
