@@ -154,10 +154,12 @@ int dt_search(const dt_index *index, const uint64_t *d_q, int64_t nq, int32_t k,
  * (the sequential search of §6.2).
  *
  * d_db: [n][64] database (n >= 1), d_q: [nq][64] queries; outputs as in
- * dt_search.  path: 0 = automatic, 1 = popcount kernel, 2 = tensor-core
- * kernel (DT_EUNSUPPORTED where not built).  Allocates scratch from the
+ * dt_search.  path: 1 = popcount kernel (CUDA cores), 2 = tensor-core
+ * kernel (tcgen05, the overlap as an FP8 0/1 contraction with exact FP32
+ * accumulation in tensor memory), 0 = automatic (2 for 64 or more queries).
+ * Both paths give identical results.  Allocates scratch from the
  * stream-ordered allocator.
- * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_EUNSUPPORTED.
+ * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA.
  */
 int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,
               uint32_t *d_idx, float *d_score, uint16_t *d_ab, int32_t path, void *stream);
@@ -204,17 +206,26 @@ int bf_search_noalloc(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int6
  * winner -1.
  *
  * d_object_of_desc: [n] uint32, indexed by original database index; ids
- *   outside [0, n_objects) cast no vote.  d_qoffsets: [nq+1] int64 device array, non-decreasing,
- *   d_qoffsets[0] = 0.  d_votes: [nq][n_objects] uint32 — the votes cast.
- * d_winner: [nq] int32.  d_consumed: [nq] int64 descriptors drawn, or NULL.
- * With T = 0 the call runs in one persistent launch and does not
- * synchronise; with T > 0 it reads the descriptor total back (synchronises).
+ *   outside [0, n_objects) cast no vote.
+ * d_qoffsets: [nq+1] int64 device array, non-decreasing, d_qoffsets[0] = 0;
+ *   n_qdesc (host) must equal d_qoffsets[nq], the number of query descriptors.
+ * d_votes: [nq][n_objects] uint32 — the votes cast.  d_winner: [nq] int32.
+ * d_consumed: [nq] int64 descriptors drawn, or NULL.
+ * engine selects how the nearest neighbours are found; every engine is
+ *   exact, so the outputs do not depend on it: 1 = Dissimilarity Tree
+ *   traversal (§4.2) of every descriptor in one persistent launch;
+ *   2 = tensor-core scan of the index's database; 0 = automatic (2 when
+ *   n_qdesc >= 256).  With T > 0, engine 2 searches the draws in rounds of
+ *   32, 64, ... per undecided query, so mostly only the draws the loop
+ *   consumes are searched.
+ * With T = 0 the call does not synchronise the stream; with T > 0 and
+ * engine 2 it reads each round's batch size back (synchronises).
  * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_ETIMEOUT.
  */
 int retrieve_objects(const dt_index *index, const uint32_t *d_object_of_desc, int32_t n_objects,
                      const uint64_t *d_qdesc, const int64_t *d_qoffsets, int32_t nq,
-                     int32_t vote_threshold, uint64_t seed, uint32_t *d_votes,
-                     int32_t *d_winner, int64_t *d_consumed, void *stream);
+                     int64_t n_qdesc, int32_t vote_threshold, uint64_t seed, uint32_t *d_votes,
+                     int32_t *d_winner, int64_t *d_consumed, int32_t engine, void *stream);
 
 /*
  * dt_sync_status — wait for `stream`, then report a device-side failure

@@ -90,7 +90,7 @@ def build_dt(force=False, verbose_ptxas=False):
     with ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = DT_SO + ".tmp%d" % os.getpid()
-    _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lcuda"])
+    _run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
     os.replace(tmp, DT_SO)
     return DT_SO
 

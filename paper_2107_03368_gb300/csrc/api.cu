@@ -171,7 +171,7 @@ int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, 
     REQUIRE_DEV(d_idx, "d_idx");
     REQUIRE_DEV(d_score, "d_score");
     if (d_ab) REQUIRE_DEV(d_ab, "d_ab");
-    if (path == 2)
+    if (path == 2 || (path == 0 && nq >= 64))
         return launch_bf_tc(d_db, n, d_q, nq, k, d_idx, d_score, d_ab, (cudaStream_t)stream);
     return launch_bf_popc(d_db, n, d_q, nq, k, d_idx, d_score, d_ab, (cudaStream_t)stream);
 }
@@ -199,14 +199,16 @@ int bf_search_noalloc(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int6
 
 int retrieve_objects(const dt_index *ix, const uint32_t *d_object_of_desc, int32_t n_objects,
                      const uint64_t *d_qdesc, const int64_t *d_qoffsets, int32_t nq,
-                     int32_t vote_threshold, uint64_t seed, uint32_t *d_votes, int32_t *d_winner,
-                     int64_t *d_consumed, void *stream)
+                     int64_t n_qdesc, int32_t vote_threshold, uint64_t seed, uint32_t *d_votes,
+                     int32_t *d_winner, int64_t *d_consumed, int32_t engine, void *stream)
 {
     g_last_error.clear();
     DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
     DT_CHECK_ARG(n_objects >= 1, "n_objects must be >= 1");
     DT_CHECK_ARG(nq >= 0, "nq must be >= 0");
+    DT_CHECK_ARG(n_qdesc >= 0 && n_qdesc < (1LL << 31), "n_qdesc out of range");
     DT_CHECK_ARG(vote_threshold >= 0, "vote_threshold must be >= 0");
+    DT_CHECK_ARG(engine >= 0 && engine <= 2, "engine must be 0, 1 or 2");
     if (nq == 0) return DT_OK;
     REQUIRE_DEV(d_object_of_desc, "d_object_of_desc");
     REQUIRE_DEV(d_qdesc, "d_qdesc");
@@ -214,8 +216,8 @@ int retrieve_objects(const dt_index *ix, const uint32_t *d_object_of_desc, int32
     REQUIRE_DEV(d_votes, "d_votes");
     REQUIRE_DEV(d_winner, "d_winner");
     if (d_consumed) REQUIRE_DEV(d_consumed, "d_consumed");
-    return launch_retrieve(ix, d_object_of_desc, n_objects, d_qdesc, d_qoffsets, nq,
-                           vote_threshold, seed, d_votes, d_winner, d_consumed,
+    return launch_retrieve(ix, d_object_of_desc, n_objects, d_qdesc, d_qoffsets, nq, n_qdesc,
+                           vote_threshold, seed, d_votes, d_winner, d_consumed, engine,
                            (cudaStream_t)stream);
 }
 

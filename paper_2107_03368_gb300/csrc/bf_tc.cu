@@ -2,26 +2,32 @@
 // tensor cores.
 //
 // O[q][t] = popc(q & t) is the dot product of two 0/1 vectors of length
-// 4096, i.e. one row of a dense Q x N x 4096 contraction.  Bits are widened
-// to FP8 E4M3 (1.0 = 0x38, 0.0 = 0x00) and multiplied by tcgen05.mma
-// (kind::f8f6f4) with FP32 accumulation in tensor memory; every partial sum
-// is an integer <= 4096 < 2^24, so the result is exact.  The epilogue turns
-// O into the Eq. 1 key (A = |q| - O, B = |t| - O) and keeps per-query top-k.
+// 4096, i.e. one row of a dense Q x N x 4096 contraction.  A set bit is
+// widened to the FP8 E4M3 value 2^-6 (byte 0x08, the smallest normal) and a
+// clear bit to 0; tcgen05.mma (kind::f8f6f4) multiplies with FP32
+// accumulation in tensor memory.  Every product is 2^-12 and a row sum is
+// O * 2^-12 with O <= 4096, which FP32 holds exactly, so O = 4096 * sum is
+// exact.  The epilogue turns O into the Eq. 1 key (A = |q| - O, B = |t| - O)
+// and keeps per-query top-k.
 //
-// Kernel organisation (one persistent CTA per SM, 9 warps):
-//   * warps 4-7 (producers): for each 128-bit K chunk, widen the chunk of
-//     256 database descriptors into a 32 KB shared-memory stage (K-major
-//     8x16-byte core matrices); the first lane of warp 4 also brings the
-//     matching 16 KB chunk of the 128 pre-widened queries with one bulk copy;
-//   * warp 8 (one thread): 4 MMAs of 128 x 256 x 32 per chunk into one of two
-//     TMEM accumulators (256 columns each), then commits to free the stage;
-//   * warps 0-3 (epilogue, one thread per query row = TMEM lane): read the
-//     finished accumulator in 32-column slices while the next tile is being
+// Kernel organisation (one persistent CTA per SM, 17 warps):
+//   * warps 8-15 (producers, one database row per thread): for each 128-bit
+//     K chunk, widen the chunk of 256 database descriptors into a 32 KB
+//     shared-memory stage (K-major 8x16-byte core matrices); each thread
+//     loads the next four chunks (64 bytes) while it widens the current
+//     ones and sums its row's |t| into shared memory.  The
+//     first lane of warp 8 also brings the matching 16 KB chunk of the 128
+//     pre-widened queries with one bulk copy (TMA engine);
+//   * warp 16 (one thread): 4 MMAs of 128 x 256 x 32 per chunk into one of
+//     two TMEM accumulators (256 columns each), then commits to free the stage;
+//   * warps 0-7 (epilogue, one thread per query row = TMEM lane, two warps
+//     per TMEM sub-partition splitting the columns): read the finished
+//     accumulator in 32-column slices while the next tile is being
 //     multiplied into the other accumulator, rank candidates, keep top-k.
 // A four-stage mbarrier ring connects producers and MMA; all waits are
-// bounded and a shared abort flag makes every role leave together.
-// Work units are (128-query tile, database split); per-split lists are merged
-// by the same kernel as the popcount path.
+// bounded and a shared abort flag makes every role leave together.  Work
+// units are (128-query tile, database split); per-split lists are merged
+// afterwards.
 #include <algorithm>
 #include <mutex>
 
@@ -40,8 +46,9 @@ constexpr int A_STAGE = TM * KC;        // 16 KB
 constexpr int B_STAGE = TN * KC;        // 32 KB
 constexpr uint32_t LBO = 128;           // next core matrix along K
 constexpr uint32_t SBO = (KC / 16) * 128;  // next 8-row group (1024 B)
-constexpr int EPI_WARPS = 4, PROD_WARPS = 4;
-constexpr int THREADS = (EPI_WARPS + PROD_WARPS + 1) * 32;
+constexpr int EPI_WARPS = 8, PROD_WARPS = TN / 32;
+constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
+constexpr int THREADS = (MMA_WARP + 1) * 32;
 constexpr uint32_t TMEM_COLS = 512;     // two 256-column FP32 accumulators
 constexpr uint32_t IDESC = idesc_e4m3_f32(TM, TN);
 
@@ -55,23 +62,30 @@ struct TcCtl {
     volatile uint32_t abort;
 };
 
-constexpr size_t SMEM_BYTES = (size_t)STAGES * (A_STAGE + B_STAGE) + sizeof(TcCtl) + 1024;
+constexpr size_t STAGE_BYTES = (size_t)STAGES * (A_STAGE + B_STAGE);
+constexpr size_t SMEM_BYTES = STAGE_BYTES + sizeof(TcCtl) + 2 * TN * 4 + 1024;
 
 __device__ uint32_t g_tc_error;  // a bounded wait gave up (DT_ETIMEOUT)
 
-// 4 bits -> 4 E4M3 bytes: byte i = 0x38 if bit i else 0.
-__device__ __forceinline__ uint32_t nib_e4m3(uint32_t nib)
+// Bit j of each byte of w -> four E4M3 bytes, 0x08 (2^-6) where the bit is
+// set: shift bit j to the byte's sign position, let prmt replicate each
+// byte's sign bit over the byte (selector nibbles 0x8-0xB), keep 0x08.
+__device__ __forceinline__ uint32_t bitplane_e4m3(uint32_t w, int j)
 {
-    return ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(w << (7 - j)));
+    return r & 0x08080808u;
 }
 
-// 32 bits -> 32 E4M3 bytes as two 16-byte pieces.
+// 32 bits -> 32 E4M3 bytes as two 16-byte pieces.  Output byte 4j + m holds
+// bit 8m + j of w.  This reorders the K positions inside a chunk, the same
+// way for queries and database, which leaves every dot product unchanged.
 __device__ __forceinline__ void widen32(uint32_t w, uint4 &lo, uint4 &hi)
 {
-    lo = make_uint4(nib_e4m3(w & 15u), nib_e4m3((w >> 4) & 15u), nib_e4m3((w >> 8) & 15u),
-                    nib_e4m3((w >> 12) & 15u));
-    hi = make_uint4(nib_e4m3((w >> 16) & 15u), nib_e4m3((w >> 20) & 15u),
-                    nib_e4m3((w >> 24) & 15u), nib_e4m3(w >> 28));
+    lo = make_uint4(bitplane_e4m3(w, 0), bitplane_e4m3(w, 1), bitplane_e4m3(w, 2),
+                    bitplane_e4m3(w, 3));
+    hi = make_uint4(bitplane_e4m3(w, 4), bitplane_e4m3(w, 5), bitplane_e4m3(w, 6),
+                    bitplane_e4m3(w, 7));
 }
 
 // Byte offset of (row, 16-byte piece j of the chunk) in a K-major stage.
@@ -118,26 +132,14 @@ __global__ void widen_queries_kernel(const uint64_t *__restrict__ q, int64_t nq,
     }
 }
 
-// |t| of every database descriptor (warp per row).
-__global__ void row_popcount_kernel(const uint64_t *__restrict__ db, int64_t n,
-                                    uint32_t *__restrict__ tpop)
-{
-    const int lane = threadIdx.x & 31;
-    int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (; r < n; r += stride) {
-        uint4 v = __ldg(reinterpret_cast<const uint4 *>(db + r * kWords) + lane);
-        uint32_t s = warp_sum(__popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w));
-        if (lane == 0) tpop[r] = s;
-    }
-}
-
-// Bounded wait that also gives up when another role aborted.
+// Bounded wait that also gives up when another role aborted.  The thread
+// sleeps inside try_wait (up to 0.5 us per poll) instead of spinning, so
+// waiting warps leave the issue slots to the working ones.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, TcCtl *ctl,
                                               uint32_t *err)
 {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
+    for (uint32_t i = 0; i < (kSpinLimit >> 4); ++i) {     // at most ~2 s
+        if (mbar_try_wait_sleep(bar, parity, 500u)) return true;
         if (ctl->abort) return false;
     }
     ctl->abort = 1u;
@@ -145,18 +147,66 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, Tc
     return false;
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
-bf_tc_kernel(const uint64_t *__restrict__ db, int64_t n, const unsigned char *__restrict__ a_exp,
-             const uint32_t *__restrict__ qpop, const uint32_t *__restrict__ tpop, int64_t nq,
-             int k, int n_mtiles, int64_t n_ntiles, int64_t tiles_per_split, int n_split,
-             uint64_t *__restrict__ partial, uint32_t *err)
+// Warp-uniform version: lane 0 waits, the verdict is broadcast.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, TcCtl *ctl, uint32_t *err,
+                                          int lane)
+{
+    bool ok = true;
+    if (lane == 0) ok = wait_or_abort(bar, parity, ctl, err);
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+}
+
+struct TcArgs {
+    const uint64_t *db;              // database rows [n][64]
+    int64_t n;
+    const unsigned char *a_exp;      // pre-widened queries
+    const uint32_t *qpop;            // |q|
+    const uint32_t *idx_map;         // row -> reported index (nullable: identity)
+    int64_t nq;
+    int k;
+    int n_mtiles;
+    int64_t n_ntiles;
+    int64_t tiles_per_split;
+    int n_split;
+    uint64_t *partial;               // [2 n_split][nq][k]: two column halves per split
+    uint32_t *err;
+};
+
+// 16 bytes (chunk c) of database row t, zeros past n.
+__device__ __forceinline__ uint4 load_bits(const TcArgs &a, int64_t t, int c)
+{
+    if (t >= a.n) return make_uint4(0, 0, 0, 0);
+    return __ldg(reinterpret_cast<const uint4 *>(a.db + t * kWords) + c);
+}
+
+// Insert a candidate into a thread's sorted top-k list (rare once the list
+// is full) and return the new k-th entry; kept out of line so the hot
+// candidate loop stays small, with the k-th entry held in registers.
+__device__ __noinline__ uint64_t list_insert(uint64_t *L, int k, uint32_t key, int64_t ti,
+                                             const uint32_t *idx_map, uint64_t worst)
+{
+    const uint32_t id = idx_map ? __ldg(idx_map + ti) : (uint32_t)ti;
+    const uint64_t cand = pack(key, id);
+    if (cand >= worst) return worst;
+    int p = k - 1;
+    while (p > 0 && L[p - 1] > cand) {
+        L[p] = L[p - 1];
+        --p;
+    }
+    L[p] = cand;
+    return L[k - 1];
+}
+
+__global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         ((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *stageA = smem;                                   // [STAGES][A_STAGE]
     unsigned char *stageB = smem + (size_t)STAGES * A_STAGE;        // [STAGES][B_STAGE]
-    TcCtl *ctl = reinterpret_cast<TcCtl *>(smem + (size_t)STAGES * (A_STAGE + B_STAGE));
+    TcCtl *ctl = reinterpret_cast<TcCtl *>(smem + STAGE_BYTES);
+    uint32_t *tpop_s = reinterpret_cast<uint32_t *>(smem + STAGE_BYTES + sizeof(TcCtl));  // [2][TN]
+    uint32_t *err = args.err;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -181,51 +231,84 @@ bf_tc_kernel(const uint64_t *__restrict__ db, int64_t n, const unsigned char *__
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
-    const int64_t total_units = (int64_t)n_mtiles * n_split;
+    const int64_t n_mtiles = args.n_mtiles;
+    const int64_t total_units = n_mtiles * args.n_split;
 
-    if (warp >= EPI_WARPS && warp < EPI_WARPS + PROD_WARPS) {
+    if (warp >= EPI_WARPS && warp < MMA_WARP) {
         // ------------------------------------------------ producers
+        // One database row per thread.  Bits are loaded 64 bytes (four chunks)
+        // at a time, one group ahead of the chunks being widened; |t| is summed
+        // on the way and left in shared memory for the epilogue.
         const int pw = warp - EPI_WARPS;
-        uint32_t g = 0;
-        for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x) {
-            const int64_t mt = u % n_mtiles, sp = u / n_mtiles;
-            const int64_t t0 = sp * tiles_per_split, t1 = min(n_ntiles, t0 + tiles_per_split);
-            for (int64_t nt = t0; nt < t1; ++nt) {
-                for (int c = 0; c < NCHUNK; ++c, ++g) {
-                    const int s = (int)(g % STAGES);
-                    const uint32_t r = g / STAGES;
-                    bool ok = true;
-                    if (lane == 0) ok = wait_or_abort(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err);
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (!ok) goto done;
-                    if (pw == 0 && lane == 0) {
-                        mbar_arrive_expect_tx(&ctl->full[s], (uint32_t)A_STAGE);
-                        bulk_g2s(stageA + (size_t)s * A_STAGE,
-                                 a_exp + ((size_t)mt * NCHUNK + c) * A_STAGE, (uint32_t)A_STAGE,
-                                 &ctl->full[s]);
-                    }
-                    unsigned char *B = stageB + (size_t)s * B_STAGE;
+        const int row = pw * 32 + lane;
+        constexpr int G = 4;                       // chunks per load group
+        uint32_t g = 0, tile = 0, tp_acc = 0;
+        int64_t u = blockIdx.x, nt = 0, t1 = 0;
+        int grp = 0;
+        if (u < total_units) {
+            const int64_t sp = u / n_mtiles;
+            nt = sp * args.tiles_per_split;
+            t1 = min(args.n_ntiles, nt + args.tiles_per_split);
+        }
+        uint4 nx[G];
 #pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const int row = pw * 64 + i * 32 + lane;
-                        const int64_t t = nt * TN + row;
-                        uint4 bits = make_uint4(0, 0, 0, 0);
-                        if (t < n) bits = __ldg(reinterpret_cast<const uint4 *>(db + t * kWords) + c);
-                        store_row_chunk(B, row, bits);
+        for (int i = 0; i < G; ++i)
+            nx[i] = u < total_units ? load_bits(args, nt * TN + row, i) : make_uint4(0, 0, 0, 0);
+        while (u < total_units) {
+            const int64_t mt = u % n_mtiles;
+            const int cur_grp = grp;
+            uint4 cu[G];
+#pragma unroll
+            for (int i = 0; i < G; ++i) cu[i] = nx[i];
+            // advance (u, nt, grp) and prefetch the next group
+            if (++grp == NCHUNK / G) {
+                grp = 0;
+                if (++nt == t1) {
+                    u += gridDim.x;
+                    if (u < total_units) {
+                        const int64_t sp = u / n_mtiles;
+                        nt = sp * args.tiles_per_split;
+                        t1 = min(args.n_ntiles, nt + args.tiles_per_split);
                     }
-                    fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&ctl->full[s]);
                 }
             }
+            if (u < total_units) {
+#pragma unroll
+                for (int i = 0; i < G; ++i) nx[i] = load_bits(args, nt * TN + row, grp * G + i);
+            }
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                const int c = cur_grp * G + i;
+                const int s = (int)(g % STAGES);
+                const uint32_t r = g / STAGES;
+                if (!warp_wait(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err, lane)) goto done;
+                if (pw == 0 && lane == 0) {
+                    mbar_arrive_expect_tx(&ctl->full[s], (uint32_t)A_STAGE);
+                    bulk_g2s(stageA + (size_t)s * A_STAGE,
+                             args.a_exp + ((size_t)mt * NCHUNK + c) * A_STAGE, (uint32_t)A_STAGE,
+                             &ctl->full[s]);
+                }
+                store_row_chunk(stageB + (size_t)s * B_STAGE, row, cu[i]);
+                tp_acc += __popc(cu[i].x) + __popc(cu[i].y) + __popc(cu[i].z) + __popc(cu[i].w);
+                if (c == NCHUNK - 1) {                 // row complete: |t| for the epilogue
+                    tpop_s[(tile & 1u) * TN + row] = tp_acc;
+                    tp_acc = 0;
+                    ++tile;
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->full[s]);
+                ++g;
+            }
         }
-    } else if (warp == EPI_WARPS + PROD_WARPS) {
+    } else if (warp == MMA_WARP) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t g = 0, t = 0;
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
                 const int64_t sp = u / n_mtiles;
-                const int64_t t0 = sp * tiles_per_split, t1 = min(n_ntiles, t0 + tiles_per_split);
+                const int64_t t0 = sp * args.tiles_per_split;
+                const int64_t t1 = min(args.n_ntiles, t0 + args.tiles_per_split);
                 for (int64_t nt = t0; nt < t1; ++nt, ++t) {
                     const uint32_t acc = t & 1u, ra = t >> 1;
                     if (!wait_or_abort(&ctl->acc_empty[acc], (ra & 1u) ^ 1u, ctl, err)) goto mma_done;
@@ -255,45 +338,50 @@ bf_tc_kernel(const uint64_t *__restrict__ db, int64_t n, const unsigned char *__
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------ epilogue (warps 0-3)
-        const int row = warp * 32 + lane;            // TMEM lane = query row of the tile
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        // ------------------------------------------------ epilogue (warps 0-7)
+        // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its sub-partition) and
+        // the column half w / 4 of each tile; each half keeps its own top-k
+        // lists, merged later like two more splits.
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane;         // TMEM lane = query row of the tile
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int k = args.k;
+        const int64_t n = args.n, nq = args.nq;
         uint64_t L[kMaxK];
         uint32_t t = 0;
         for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x) {
             const int64_t mt = u % n_mtiles, sp = u / n_mtiles;
-            const int64_t t0 = sp * tiles_per_split, t1 = min(n_ntiles, t0 + tiles_per_split);
+            const int64_t t0 = sp * args.tiles_per_split;
+            const int64_t t1 = min(args.n_ntiles, t0 + args.tiles_per_split);
             const int64_t qi = mt * TM + row;
-            const QueryWeights w = query_weights(qi < nq ? qpop[qi] : 0u);
+            const QueryWeights w = query_weights(qi < nq ? args.qpop[qi] : 0u);
+            // key = A*Z + B*P = (|q| - O) Z + (|t| - O) P = |t| P + |q| Z - O (Z + P)
+            const uint32_t qz = w.pop * w.Z, zp = w.Z + w.P;
             for (int j = 0; j < k; ++j) L[j] = kEmpty;
             uint64_t worst = kEmpty;
+            uint32_t wkey = 0xFFFFFFFFu;      // key part of `worst`
             for (int64_t nt = t0; nt < t1; ++nt, ++t) {
                 const uint32_t acc = t & 1u, ra = t >> 1;
-                bool ok = true;
-                if (lane == 0) ok = wait_or_abort(&ctl->acc_full[acc], ra & 1u, ctl, err);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) goto done;
+                if (!warp_wait(&ctl->acc_full[acc], ra & 1u, ctl, err, lane)) goto done;
                 tc_fence_after();
                 const int64_t base = nt * TN;
-                for (int cb = 0; cb < TN / 32; ++cb) {
+                for (int cb = half * (TN / 64); cb < (half + 1) * (TN / 64); ++cb) {
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(lane_base + acc * (uint32_t)TN + cb * 32, v);
                     tmem_ld_wait();
+                    const int64_t b0 = base + cb * 32;
+                    const int m = (int)(n - b0 < 32 ? n - b0 : 32);
+                    const uint32_t *tp = tpop_s + (t & 1u) * TN + cb * 32;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int64_t ti = base + cb * 32 + j;
-                        if (ti >= n) break;
-                        // exact integer held in an FP32: add 2^23, read the mantissa
-                        const uint32_t o = __float_as_uint(__uint_as_float(v[j]) + 8388608.0f) - 0x4B000000u;
-                        const uint64_t cand = pack(pair_key(w, o, __ldg(tpop + ti)), (uint32_t)ti);
-                        if (cand < worst) {
-                            int p = k - 1;
-                            while (p > 0 && L[p - 1] > cand) {
-                                L[p] = L[p - 1];
-                                --p;
-                            }
-                            L[p] = cand;
-                            worst = L[k - 1];
+                        // sum = O * 2^-12 exactly: 4096 * sum + 2^23, read the mantissa
+                        const uint32_t o =
+                            __float_as_uint(fmaf(__uint_as_float(v[j]), 4096.0f, 8388608.0f)) -
+                            0x4B000000u;
+                        const uint32_t key = tp[j] * w.P + qz - o * zp;
+                        if (j < m && key <= wkey) {   // rare once the list has filled
+                            worst = list_insert(L, k, key, b0 + j, args.idx_map, worst);
+                            wkey = (uint32_t)(worst >> 32);
                         }
                     }
                 }
@@ -302,7 +390,8 @@ bf_tc_kernel(const uint64_t *__restrict__ db, int64_t n, const unsigned char *__
                 if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
             }
             if (qi < nq)
-                for (int j = 0; j < k; ++j) partial[((int64_t)sp * nq + qi) * k + j] = L[j];
+                for (int j = 0; j < k; ++j)
+                    args.partial[((int64_t)(2 * sp + half) * nq + qi) * k + j] = L[j];
         }
     }
 done:
@@ -314,19 +403,26 @@ done:
     }
 }
 
-}  // namespace
-
-int take_tc_error(bool *raised)
+// One warp per query: the smallest entry over the split lists -> its index.
+__global__ void merge_top1_kernel(const uint64_t *__restrict__ partial, int n_split, int64_t nq,
+                                  uint32_t *__restrict__ nn)
 {
-    uint32_t v = 0, zero = 0;
-    DT_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(v)));
-    if (v) DT_CUDA_TRY(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(zero)));
-    *raised = v != 0;
-    return DT_OK;
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    uint64_t best = kEmpty;
+    for (int s = lane; s < n_split; s += 32) {
+        uint64_t v = partial[(int64_t)s * nq + q];
+        best = v < best ? v : best;
+    }
+    best = warp_min_u64(best);
+    if (lane == 0) nn[q] = best == kEmpty ? 0xFFFFFFFFu : (uint32_t)best;
 }
 
-int launch_bf_tc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
-                 uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s)
+// Per-split top-k lists of every query over db (rows reported through
+// idx_map when given).  *partial is allocated on the stream; the caller frees it.
+int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
+                    int64_t nq, int k, cudaStream_t s, uint64_t **partial_out, int *n_split_out)
 {
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
@@ -345,29 +441,71 @@ int launch_bf_tc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, i
     const int grid = (int)std::min<int64_t>(units, sms);
 
     unsigned char *a_exp = nullptr;
-    uint32_t *qpop = nullptr, *tpop = nullptr, *err = nullptr;
+    uint32_t *qpop = nullptr, *err = nullptr;
     uint64_t *partial = nullptr;
     const size_t a_bytes = (size_t)n_mtiles * NCHUNK * A_STAGE;
     DT_CUDA_TRY(cudaMallocAsync((void **)&a_exp, a_bytes, s));
     DT_CUDA_TRY(cudaMallocAsync((void **)&qpop, (size_t)nq * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&tpop, (size_t)n * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)n_split * nq * k * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)2 * n_split * nq * k * 8, s));
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
-    {
-        const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
-        widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, nq, n_mtiles, a_exp, qpop);
-        row_popcount_kernel<<<(unsigned)std::min<int64_t>((n + 7) / 8, 32 * 152), 256, 0, s>>>(db, n, tpop);
-        DT_CUDA_TRY(cudaGetLastError());
-    }
-    bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(db, n, a_exp, qpop, tpop, nq, k, n_mtiles,
-                                                   n_ntiles, tiles_per_split, n_split, partial, err);
+    const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
+    widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, nq, n_mtiles, a_exp, qpop);
     DT_CUDA_TRY(cudaGetLastError());
-    int rc = launch_merge_partials(partial, n_split, db, q, nq, k, idx, score, ab, s);
-    cudaFreeAsync(partial, s);
-    cudaFreeAsync(tpop, s);
+    TcArgs a;
+    a.db = db;
+    a.n = n;
+    a.a_exp = a_exp;
+    a.qpop = qpop;
+    a.idx_map = idx_map;
+    a.nq = nq;
+    a.k = k;
+    a.n_mtiles = n_mtiles;
+    a.n_ntiles = n_ntiles;
+    a.tiles_per_split = tiles_per_split;
+    a.n_split = n_split;
+    a.partial = partial;
+    a.err = err;
+    bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
+    DT_CUDA_TRY(cudaGetLastError());
     cudaFreeAsync(qpop, s);
     cudaFreeAsync(a_exp, s);
+    *partial_out = partial;
+    *n_split_out = 2 * n_split;
+    return DT_OK;
+}
+
+}  // namespace
+
+int take_tc_error(bool *raised)
+{
+    uint32_t v = 0, zero = 0;
+    DT_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(v)));
+    if (v) DT_CUDA_TRY(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(zero)));
+    *raised = v != 0;
+    return DT_OK;
+}
+
+int launch_bf_tc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                 uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s)
+{
+    uint64_t *partial = nullptr;
+    int n_split = 0;
+    if (int r = tc_partial_topk(db, n, nullptr, q, nq, k, s, &partial, &n_split)) return r;
+    int rc = launch_merge_partials(partial, n_split, db, q, nq, k, idx, score, ab, s);
+    cudaFreeAsync(partial, s);
     return rc;
+}
+
+int launch_tc_top1(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
+                   int64_t nq, uint32_t *nn, cudaStream_t s)
+{
+    uint64_t *partial = nullptr;
+    int n_split = 0;
+    if (int r = tc_partial_topk(db, n, idx_map, q, nq, 1, s, &partial, &n_split)) return r;
+    merge_top1_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(partial, n_split, nq, nn);
+    DT_CUDA_TRY(cudaGetLastError());
+    cudaFreeAsync(partial, s);
+    return DT_OK;
 }
 
 }  // namespace dtk

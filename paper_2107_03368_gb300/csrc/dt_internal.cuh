@@ -176,7 +176,11 @@ int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fu
 int launch_dt_search(const dt_index *ix, const uint64_t *q, int64_t nq, int k, uint32_t *idx,
                      float *score, uint16_t *ab, dt_stats *stats, cudaStream_t s);
 int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects,
-                    const uint64_t *qdesc, const int64_t *qoffsets, int nq, int threshold,
-                    uint64_t seed, uint32_t *votes, int32_t *winner, int64_t *consumed,
-                    cudaStream_t s);
+                    const uint64_t *qdesc, const int64_t *qoffsets, int nq, int64_t total,
+                    int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
+                    int64_t *consumed, int engine, cudaStream_t s);
+// Exact top-1 of each query over db on the tensor cores; reported indices go
+// through idx_map when given (ties are broken on the reported index).
+int launch_tc_top1(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
+                   int64_t nq, uint32_t *nn, cudaStream_t s);
 }  // namespace dtk

@@ -1,19 +1,30 @@
 // votes.cu — partial-object retrieval by voting (§3).
 //
-// Every descriptor of every partial query is one work item of a persistent
-// launch (warps take items from an atomic counter; a binary search over the
-// CSR offsets finds the item's query), so uneven queries of 500..10,000
-// descriptors share one launch.  Each item's nearest database descriptor is
-// found with the tree traversal of dt_search (k = 1).
+// Query j's descriptors are drawn in a random order (Fisher-Yates from the
+// last position, SplitMix64 seeded with the (j+1)-th output of
+// SplitMix64(seed)); each drawn descriptor's nearest database descriptor
+// (exact top-1 of Eq. 1, ties by lowest original index) votes for its
+// object; with a threshold T the first object to reach T votes wins.
 //
-// Threshold 0: every descriptor votes; the vote is an atomic increment of
-// votes[query][object] straight from the traversal kernel, and a second
-// kernel picks each query's winner.  Threshold T > 0: the nearest neighbours
-// are kept, then one thread per query draws the query's descriptors in its
-// Fisher-Yates / SplitMix64 order and replays the votes until an object
-// reaches T.
+// Two engines find the nearest neighbours; both are exact, so both give the
+// same votes:
+//  * tree: every descriptor is one work item of a persistent launch (warps
+//    take items from an atomic counter, a binary search over the CSR
+//    offsets finds the item's query) traversing the Dissimilarity Tree as in
+//    dt_search.  With T = 0 the vote is an atomic increment straight from
+//    the traversal kernel; with T > 0 all neighbours are kept and one thread
+//    per query replays the draw order.
+//  * tensor: batches of descriptors are scanned against the index's
+//    tree-ordered database on the tensor cores (bf_tc.cu, rows reported as
+//    original indices).  With T = 0 all descriptors form one batch.  With
+//    T > 0 the draws are taken in rounds — the next 32, 64, 128 ... drawn
+//    descriptors of every undecided query — and a replay kernel advances
+//    each query's vote count in draw order, so only the descriptors the
+//    loop of §3 actually consumes (plus the rest of their round) are searched.
 #include <algorithm>
+#include <vector>
 
+#include "block_util.cuh"
 #include "dt_internal.cuh"
 #include "dt_traverse.cuh"
 
@@ -38,6 +49,15 @@ __device__ __forceinline__ int find_query(const int64_t *__restrict__ off, int n
     return lo;
 }
 
+__device__ __forceinline__ uint64_t splitmix_next(uint64_t &s)
+{
+    uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------- tree engine
 // mode 0: vote directly; mode 1: store the neighbour's original index.
 template <bool USE_AND, int MODE>
 __global__ void __launch_bounds__(VT)
@@ -100,21 +120,9 @@ __global__ void winner_kernel(const uint32_t *__restrict__ votes, int n_objects,
     }
 }
 
-__device__ __forceinline__ uint64_t splitmix_next(uint64_t &s)
-{
-    uint64_t z = (s += 0x9e3779b97f4a7c15ull);
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return z ^ (z >> 31);
-}
-
-// One thread per query: draw order (Fisher-Yates from the last position,
-// SplitMix64 seeded with the (j+1)-th output of SplitMix64(seed)), then the
-// vote replay of §3 up to the threshold.
-__global__ void replay_kernel(const uint32_t *__restrict__ nn, const uint32_t *__restrict__ object_of,
-                              int n_objects, const int64_t *__restrict__ qoff, int nq, int threshold,
-                              uint64_t seed, uint32_t *__restrict__ order, uint32_t *__restrict__ votes,
-                              int32_t *__restrict__ winner, int64_t *__restrict__ consumed)
+// Query j's draw order into order[qoff[j] ..].
+__global__ void draw_order_kernel(const int64_t *__restrict__ qoff, int nq, uint64_t seed,
+                                  uint32_t *__restrict__ order)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nq) return;
@@ -129,6 +137,18 @@ __global__ void replay_kernel(const uint32_t *__restrict__ nn, const uint32_t *_
         ord[i] = ord[r];
         ord[r] = t;
     }
+}
+
+// One thread per query: the vote loop of §3 over all draws (tree engine, T > 0).
+__global__ void replay_kernel(const uint32_t *__restrict__ nn, const uint32_t *__restrict__ object_of,
+                              int n_objects, const int64_t *__restrict__ qoff, int nq, int threshold,
+                              const uint32_t *__restrict__ order, uint32_t *__restrict__ votes,
+                              int32_t *__restrict__ winner, int64_t *__restrict__ consumed)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    const int64_t b = qoff[j], m = max((int64_t)0, qoff[j + 1] - b);
+    const uint32_t *ord = order + b;
     uint32_t *v = votes + (int64_t)j * n_objects;
     int32_t win = -1;
     int64_t used = 0;
@@ -153,40 +173,134 @@ __global__ void replay_kernel(const uint32_t *__restrict__ nn, const uint32_t *_
     if (consumed) consumed[j] = used;
 }
 
-}  // namespace
+// -------------------------------------------------------------- tensor engine
+// T = 0: one vote per descriptor from its neighbour.
+__global__ void vote_all_kernel(const uint32_t *__restrict__ nn, int64_t total,
+                                const uint32_t *__restrict__ object_of, int n_objects,
+                                const int64_t *__restrict__ qoff, int nq, uint32_t *__restrict__ votes)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < total; i += stride) {
+        const uint32_t t = nn[i];
+        if (t == 0xFFFFFFFFu) continue;
+        const uint32_t o = __ldg(object_of + t);
+        if (o >= (uint32_t)n_objects) continue;
+        atomicAdd(&votes[(int64_t)find_query(qoff, nq, i) * n_objects + o], 1u);
+    }
+}
 
-int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects,
-                    const uint64_t *qdesc, const int64_t *qoffsets, int nq, int threshold,
-                    uint64_t seed, uint32_t *votes, int32_t *winner, int64_t *consumed,
-                    cudaStream_t s)
+struct RoundState {
+    int64_t *used;       // draws consumed so far
+    int32_t *done;       // 1 once decided or out of draws
+    int64_t *take;       // draws in this round
+    int64_t *slot;       // first batch slot of this round (exclusive scan of take)
+    int64_t *total;      // [1] batch size of this round
+};
+
+// take_j = undecided ? min(C, m_j - used_j) : 0, then an exclusive scan in one block.
+__global__ void round_plan_kernel(const int64_t *__restrict__ qoff, int nq, int64_t C, RoundState st)
+{
+    __shared__ uint32_t scan_tmp[33];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nq; base += blockDim.x) {
+        const int j = base + threadIdx.x;
+        int64_t t = 0;
+        if (j < nq && !st.done[j]) t = min(C, (qoff[j + 1] - qoff[j]) - st.used[j]);
+        if (j < nq) st.take[j] = t;
+        uint32_t tot;
+        const uint32_t ex = block_excl_scan((uint32_t)t, scan_tmp, &tot);
+        if (j < nq) st.slot[j] = (int64_t)carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st.total[0] = (int64_t)carry;
+}
+
+// Warp per query: copy this round's drawn descriptors into the batch.
+__global__ void round_gather_kernel(const uint64_t *__restrict__ qdesc, const int64_t *__restrict__ qoff,
+                                    int nq, const uint32_t *__restrict__ order, RoundState st,
+                                    uint64_t *__restrict__ batch)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (j >= nq) return;
+    const int64_t take = st.take[j], b = qoff[j], u = st.used[j], s0 = st.slot[j];
+    for (int64_t i = 0; i < take; ++i) {
+        const int64_t src = b + order[b + u + i];
+        reinterpret_cast<uint4 *>(batch + (s0 + i) * kWords)[lane] =
+            __ldg(reinterpret_cast<const uint4 *>(qdesc + src * kWords) + lane);
+    }
+}
+
+// Thread per query: advance the vote loop through this round's draws.
+__global__ void round_replay_kernel(const uint32_t *__restrict__ nn, const uint32_t *__restrict__ object_of,
+                                    int n_objects, const int64_t *__restrict__ qoff, int nq,
+                                    int threshold, RoundState st, uint32_t *__restrict__ votes,
+                                    int32_t *__restrict__ winner)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq || st.done[j]) return;
+    const int64_t take = st.take[j], s0 = st.slot[j], m = qoff[j + 1] - qoff[j];
+    uint32_t *v = votes + (int64_t)j * n_objects;
+    int64_t used = st.used[j];
+    for (int64_t i = 0; i < take; ++i) {
+        const uint32_t t = nn[s0 + i];
+        ++used;
+        if (t == 0xFFFFFFFFu) continue;
+        const uint32_t o = object_of[t];
+        if (o >= (uint32_t)n_objects) continue;
+        if (++v[o] == (uint32_t)threshold) {
+            winner[j] = (int32_t)o;
+            st.done[j] = 1;
+            break;
+        }
+    }
+    st.used[j] = used;
+    if (used >= m) st.done[j] = 1;
+}
+
+// Queries that ran out of draws: most votes, lowest id; report draws used.
+__global__ void round_finish_kernel(const uint32_t *__restrict__ votes, int n_objects, int nq,
+                                    RoundState st, int32_t *__restrict__ winner,
+                                    int64_t *__restrict__ consumed)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    if (winner[j] < 0) {
+        const uint32_t *v = votes + (int64_t)j * n_objects;
+        uint32_t best = 0;
+        int32_t win = -1;
+        for (int o = 0; o < n_objects; ++o)
+            if (v[o] > best) { best = v[o]; win = o; }
+        winner[j] = win;
+    }
+    if (consumed) consumed[j] = st.used[j];
+}
+
+int retrieve_tree(const dt_index *ix, const uint32_t *object_of, int n_objects, const uint64_t *qdesc,
+                  const int64_t *qoffsets, int nq, int64_t total, int threshold, uint64_t seed,
+                  uint32_t *votes, int32_t *winner, int64_t *consumed, cudaStream_t s)
 {
     TreeView tv{ix->node, ix->or_img, ix->and_img, ix->db_tree, ix->perm};
     const bool use_and = ix->use_and != 0;
-    DT_CUDA_TRY(cudaMemsetAsync(votes, 0, (size_t)nq * n_objects * 4, s));
     const int stack_cap = ix->depth + 2;
-
-    int64_t total = -1;
     uint32_t *nn = nullptr, *order = nullptr;
     if (threshold > 0) {
-        DT_CUDA_TRY(cudaMemcpyAsync(&total, qoffsets + nq, 8, cudaMemcpyDeviceToHost, s));
-        DT_CUDA_TRY(cudaStreamSynchronize(s));
-        if (total < 0) {
-            set_error("retrieve_objects: negative descriptor total");
-            return DT_EINVAL;
-        }
         DT_CUDA_TRY(cudaMallocAsync((void **)&nn, (size_t)std::max<int64_t>(total, 1) * 4, s));
         DT_CUDA_TRY(cudaMallocAsync((void **)&order, (size_t)std::max<int64_t>(total, 1) * 4, s));
     }
-
     auto k0 = use_and ? retrieve_nn_kernel<true, 0> : retrieve_nn_kernel<false, 0>;
     auto k1 = use_and ? retrieve_nn_kernel<true, 1> : retrieve_nn_kernel<false, 1>;
     auto kern = threshold > 0 ? k1 : k0;
     int per_sm = 0;
     DT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, VT, 0));
     int64_t blocks = std::max(1, per_sm) * (int64_t)sm_count();
-    if (total >= 0) blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (total + 7) / 8));
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (total + 7) / 8));
     const int64_t nwarps = blocks * (VT / 32);
-
     VoteCtl *ctl = nullptr;
     uint64_t *stacks = nullptr;
     DT_CUDA_TRY(cudaMallocAsync((void **)&ctl, sizeof(VoteCtl), s));
@@ -196,9 +310,9 @@ int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects
                                          stack_cap, ctl, votes, nn);
     DT_CUDA_TRY(cudaGetLastError());
     if (threshold > 0) {
+        draw_order_kernel<<<(nq + 127) / 128, 128, 0, s>>>(qoffsets, nq, seed, order);
         replay_kernel<<<(nq + 127) / 128, 128, 0, s>>>(nn, object_of, n_objects, qoffsets, nq,
-                                                      threshold, seed, order, votes, winner,
-                                                      consumed);
+                                                      threshold, order, votes, winner, consumed);
     } else {
         winner_kernel<<<(nq + 7) / 8, 256, 0, s>>>(votes, n_objects, qoffsets, nq, winner, consumed);
     }
@@ -208,6 +322,97 @@ int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects
     if (nn) DT_CUDA_TRY(cudaFreeAsync(nn, s));
     if (order) DT_CUDA_TRY(cudaFreeAsync(order, s));
     return DT_OK;
+}
+
+int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects,
+                    const uint64_t *qdesc, const int64_t *qoffsets, int nq, int64_t total,
+                    int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
+                    int64_t *consumed, cudaStream_t s)
+{
+    if (threshold == 0) {
+        uint32_t *nn = nullptr;
+        DT_CUDA_TRY(cudaMallocAsync((void **)&nn, (size_t)std::max<int64_t>(total, 1) * 4, s));
+        if (total > 0) {
+            if (int r = launch_tc_top1(ix->db_tree, ix->n, ix->perm, qdesc, total, nn, s)) return r;
+            vote_all_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(
+                nn, total, object_of, n_objects, qoffsets, nq, votes);
+        }
+        winner_kernel<<<(nq + 7) / 8, 256, 0, s>>>(votes, n_objects, qoffsets, nq, winner, consumed);
+        DT_CUDA_TRY(cudaGetLastError());
+        DT_CUDA_TRY(cudaFreeAsync(nn, s));
+        return DT_OK;
+    }
+    // rounds of draws
+    uint32_t *order = nullptr;
+    RoundState st;
+    DT_CUDA_TRY(cudaMallocAsync((void **)&order, (size_t)std::max<int64_t>(total, 1) * 4, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&st.used, (size_t)nq * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&st.done, (size_t)nq * 4, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&st.take, (size_t)nq * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&st.slot, (size_t)nq * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&st.total, 8, s));
+    DT_CUDA_TRY(cudaMemsetAsync(st.used, 0, (size_t)nq * 8, s));
+    DT_CUDA_TRY(cudaMemsetAsync(st.done, 0, (size_t)nq * 4, s));
+    DT_CUDA_TRY(cudaMemsetAsync(winner, 0xFF, (size_t)nq * 4, s));   // -1
+    draw_order_kernel<<<(nq + 127) / 128, 128, 0, s>>>(qoffsets, nq, seed, order);
+    DT_CUDA_TRY(cudaGetLastError());
+    int rc = DT_OK;
+    int64_t C = std::max<int64_t>(32, 2 * (int64_t)threshold);
+    for (;;) {
+        round_plan_kernel<<<1, 1024, 0, s>>>(qoffsets, nq, C, st);
+        int64_t batch_n = 0;
+        cudaError_t e = cudaMemcpyAsync(&batch_n, st.total, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error(std::string("retrieve_objects round: ") + cudaGetErrorString(e));
+            rc = DT_ECUDA;
+            break;
+        }
+        if (batch_n == 0) break;
+        uint64_t *batch = nullptr;
+        uint32_t *nn = nullptr;
+        if (cudaMallocAsync((void **)&batch, (size_t)batch_n * 512, s) != cudaSuccess ||
+            cudaMallocAsync((void **)&nn, (size_t)batch_n * 4, s) != cudaSuccess) {
+            set_error("retrieve_objects: batch allocation failed");
+            rc = DT_ENOMEM;
+            break;
+        }
+        round_gather_kernel<<<(nq + 7) / 8, 256, 0, s>>>(qdesc, qoffsets, nq, order, st, batch);
+        rc = launch_tc_top1(ix->db_tree, ix->n, ix->perm, batch, batch_n, nn, s);
+        if (rc == DT_OK)
+            round_replay_kernel<<<(nq + 127) / 128, 128, 0, s>>>(nn, object_of, n_objects, qoffsets,
+                                                                nq, threshold, st, votes, winner);
+        cudaFreeAsync(nn, s);
+        cudaFreeAsync(batch, s);
+        if (rc != DT_OK) break;
+        C *= 2;
+    }
+    if (rc == DT_OK)
+        round_finish_kernel<<<(nq + 127) / 128, 128, 0, s>>>(votes, n_objects, nq, st, winner, consumed);
+    cudaFreeAsync(st.total, s);
+    cudaFreeAsync(st.slot, s);
+    cudaFreeAsync(st.take, s);
+    cudaFreeAsync(st.done, s);
+    cudaFreeAsync(st.used, s);
+    cudaFreeAsync(order, s);
+    DT_CUDA_TRY(cudaGetLastError());
+    return rc;
+}
+
+}  // namespace
+
+int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects,
+                    const uint64_t *qdesc, const int64_t *qoffsets, int nq, int64_t total,
+                    int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
+                    int64_t *consumed, int engine, cudaStream_t s)
+{
+    DT_CUDA_TRY(cudaMemsetAsync(votes, 0, (size_t)nq * n_objects * 4, s));
+    if (engine == 0) engine = total >= 256 ? 2 : 1;
+    if (engine == 2)
+        return retrieve_tensor(ix, object_of, n_objects, qdesc, qoffsets, nq, total, threshold, seed,
+                               votes, winner, consumed, s);
+    return retrieve_tree(ix, object_of, n_objects, qdesc, qoffsets, nq, total, threshold, seed, votes,
+                         winner, consumed, s);
 }
 
 }  // namespace dtk

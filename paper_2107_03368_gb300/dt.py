@@ -69,7 +69,8 @@ def load():
             "dt_search": ([P, P, i64, i32, P, P, P, P, P], ctypes.c_int),
             "bf_search": ([P, i64, P, i64, i32, P, P, P, i32, P], ctypes.c_int),
             "bf_search_noalloc": ([P, i64, P, i64, i32, P, P, P, P], ctypes.c_int),
-            "retrieve_objects": ([P, P, i32, P, P, i32, i32, u64, P, P, P, P], ctypes.c_int),
+            "retrieve_objects": ([P, P, i32, P, P, i32, i64, i32, u64, P, P, P, i32, P],
+                                 ctypes.c_int),
             "dt_sync_status": ([P], ctypes.c_int),
             "dt_free": ([P], None),
             "dt_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -202,9 +203,10 @@ def bf_search_noalloc(db, q, k, out, stream=None):
 
 
 def retrieve_objects(index: Index, object_of, n_objects, qdesc, qoffsets, vote_threshold=0,
-                     seed=0, with_consumed=True, out=None, stream=None):
+                     seed=0, with_consumed=True, engine=0, out=None, stream=None):
     """Returns (votes int32 [nq, n_objects] (uint32 counts), winner int32 [nq],
-    consumed int64 [nq] or None)."""
+    consumed int64 [nq] or None).  engine: 0 auto, 1 tree traversal,
+    2 tensor-core scan (identical results)."""
     qdesc = _desc(qdesc, "qdesc")
     if not (object_of.is_cuda and object_of.dtype == torch.int32 and object_of.is_contiguous()):
         raise ValueError("object_of must be a contiguous CUDA int32 tensor")
@@ -219,8 +221,9 @@ def retrieve_objects(index: Index, object_of, n_objects, qdesc, qoffsets, vote_t
     else:
         votes, winner, consumed = out
     _check(load().retrieve_objects(index.handle, _ptr(object_of), n_objects, _ptr(qdesc),
-                                   _ptr(qoffsets), nq, vote_threshold, ctypes.c_uint64(seed),
-                                   _ptr(votes), _ptr(winner), _ptr(consumed), _stream(stream)),
+                                   _ptr(qoffsets), nq, qdesc.shape[0], vote_threshold,
+                                   ctypes.c_uint64(seed), _ptr(votes), _ptr(winner),
+                                   _ptr(consumed), engine, _stream(stream)),
            "retrieve_objects")
     return votes, winner, consumed
 

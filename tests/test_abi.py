@@ -54,6 +54,6 @@ def test_bad_sizes_are_rejected():
     assert lib.dt_build(None, 0, None, None, ctypes.byref(out)) == dt.DT_EINVAL
     assert lib.bf_search(None, 0, None, 5, 1, None, None, None, 0, None) == dt.DT_EINVAL
     assert lib.bf_search(None, 10, None, 5, 1, None, None, None, 7, None) == dt.DT_EINVAL
-    assert lib.retrieve_objects(None, None, 3, None, None, 1, 0, 0, None, None, None,
+    assert lib.retrieve_objects(None, None, 3, None, None, 1, 10, 0, 0, None, None, None, 0,
                                 None) == dt.DT_EINVAL
     assert lib.dt_get_info(None, None) == dt.DT_EINVAL

@@ -75,6 +75,8 @@ def test_sampled_nodes_structure(big):
 
 
 def test_partial_retrieval_on_full_database():
+    """Threshold 0 on a subset of uneven queries with both engines; threshold
+    10 on all 1,000 queries with the round-based tensor engine."""
     n_obj, per = 400, 25_000
     db, obj = synth.database(SEED + 2, n_obj * per, per_object=per)
     qd, off, qobj = synth.partial_queries(SEED + 2, db, n_obj, per, 1000)
@@ -88,7 +90,12 @@ def test_partial_retrieval_on_full_database():
     d_obj = torch.from_numpy(obj.view(np.int32)).cuda()
     d_qd = to_dev(qd_s)
     votes, winner, consumed = dt.retrieve_objects(ix, d_obj, n_obj, d_qd,
-                                                  torch.from_numpy(off_s).cuda(), 0, SEED)
+                                                  torch.from_numpy(off_s).cuda(), 0, SEED, engine=2)
+    votes_t, winner_t, consumed_t = dt.retrieve_objects(ix, d_obj, n_obj, d_qd,
+                                                        torch.from_numpy(off_s).cuda(), 0, SEED,
+                                                        engine=1)
+    assert torch.equal(votes, votes_t) and torch.equal(winner, winner_t)
+    assert torch.equal(consumed, consumed_t)
     b_idx, _, _ = dt.bf_search(d_db, d_qd, 1)
     nn = idx_np(b_idx)[:, 0]
     v = votes.cpu().numpy().view(np.uint32)
@@ -101,11 +108,26 @@ def test_partial_retrieval_on_full_database():
     pick = np.linspace(0, qd_s.shape[0] - 1, 8).astype(np.int64)
     o_idx, _, _ = oracle.bf_topk(db, qd_s[pick], 1)
     assert np.array_equal(nn[pick], o_idx[:, 0])
-    # threshold 10: the winner reaches exactly 10 votes within the draws
-    votes10, winner10, used10 = dt.retrieve_objects(ix, d_obj, n_obj, d_qd,
-                                                    torch.from_numpy(off_s).cuda(), 10, SEED)
+    # threshold 10, subset: both engines agree
+    r2 = dt.retrieve_objects(ix, d_obj, n_obj, d_qd, torch.from_numpy(off_s).cuda(), 10, SEED,
+                             engine=2)
+    r1 = dt.retrieve_objects(ix, d_obj, n_obj, d_qd, torch.from_numpy(off_s).cuda(), 10, SEED,
+                             engine=1)
+    for x, y in zip(r1, r2):
+        assert torch.equal(x, y)
+    # threshold 10 on all 1,000 partial queries: the winner reaches exactly 10
+    # votes, every vote is a draw, and the draws replay the oracle's order
+    votes10, winner10, used10 = dt.retrieve_objects(ix, d_obj, n_obj, to_dev(qd),
+                                                    torch.from_numpy(off).cuda(), 10, SEED,
+                                                    engine=2)
     v10 = votes10.cpu().numpy().view(np.uint32)
-    for j in range(sub):
-        w = winner10[j].item()
-        assert v10[j, w] == 10 and v10[j].sum() == used10[j].item() <= sizes[j]
+    w10, u10 = winner10.cpu().numpy(), used10.cpu().numpy()
+    assert np.all(v10[np.arange(len(w10)), w10] == 10)
+    assert np.array_equal(v10.sum(1), u10) and np.all(u10 <= np.diff(off))
+    assert (w10 == qobj).mean() > 0.95
+    j = 7                                   # replay one query by hand
+    order = oracle.permutation(SEED, j, int(off[j + 1] - off[j]))[: u10[j]]
+    o_nn, _, _ = oracle.bf_topk(db, qd[off[j] + order], 1)
+    expect = np.bincount(obj[o_nn[:, 0]], minlength=n_obj)
+    assert np.array_equal(v10[j], expect)
     ix.free()

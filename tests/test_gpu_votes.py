@@ -11,8 +11,9 @@ from paper_2107_03368_gb300 import dt, synth
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("threshold", [0, 1, 3, 10, 100000])
-def test_votes_match_oracle(threshold):
+def test_votes_match_oracle(threshold, engine):
     seed = 77
     n_obj, per = 12, 150
     db, obj = synth.database(seed, n_obj * per, per_object=per, pool=10)
@@ -23,7 +24,7 @@ def test_votes_match_oracle(threshold):
     ix = dt.dt_build(to_dev(db))
     votes, winner, consumed = dt.retrieve_objects(
         ix, torch.from_numpy(obj.view(np.int32)).cuda(), n_obj, to_dev(qd),
-        torch.from_numpy(off).cuda(), threshold, seed)
+        torch.from_numpy(off).cuda(), threshold, seed, engine=engine)
     assert np.array_equal(votes.cpu().numpy().view(np.uint32), ov)
     assert np.array_equal(winner.cpu().numpy(), ow)
     assert np.array_equal(consumed.cpu().numpy(), oc)
