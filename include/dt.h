@@ -235,6 +235,32 @@ int retrieve_objects(const dt_index *index, const uint32_t *d_object_of_desc, in
  */
 int dt_sync_status(void *stream);
 
+/*
+ * dt_autotune — pick launch shapes by timing them on the caller's data.
+ * The paper has no counterpart; results never depend on the shapes, only
+ * speed.  With `index`, the tree traversal's threads per block and resident
+ * blocks per SM are tuned for (index->n, nq, k); with `d_db`, the database
+ * split counts of both brute-force paths are tuned for (n, nq, k).  The
+ * winners go into a process-wide table keyed by (kind, log2 n, log2 nq, k,
+ * SM count) that later calls of the same shape use.  Runs each candidate
+ * twice (synchronises the stream).  `report` (nullable, host) receives the
+ * chosen shapes and their times.  Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA.
+ */
+typedef struct {
+    int32_t tree_threads, tree_blocks_per_sm;
+    int32_t popc_splits, tc_splits;
+    float tree_ms, popc_ms, tc_ms;
+    int32_t candidates_timed;
+} dt_tune_report;
+int dt_autotune(const dt_index *index, const uint64_t *d_db, int64_t n, const uint64_t *d_q,
+                int64_t nq, int32_t k, void *stream, dt_tune_report *report);
+
+/* Save the tuning table to a text file / load one (returns the number of
+ * entries loaded, or a negative status) / forget all entries. */
+int dt_tune_save(const char *path);
+int dt_tune_load(const char *path);
+void dt_tune_clear(void);
+
 /* Release an index (NULL is allowed).  Synchronises the device it lives on. */
 void dt_free(dt_index *index);
 

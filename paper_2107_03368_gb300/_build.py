@@ -23,6 +23,7 @@ OBJ_DIR = os.path.join(HERE, "_build")
 
 CUDA_SOURCES = [
     "api.cu",
+    "autotune.cu",
     "bf_popc.cu",
     "bf_tc.cu",
     "dt_build.cu",

@@ -1,0 +1,207 @@
+// autotune.cu — launch-shape autotuner for the search kernels.
+//
+// Knobs (none changes a result, only speed):
+//   TREE   dt_search traversal: threads per block (128 or 256) and resident
+//          blocks per SM of the persistent grid (how many queries are in
+//          flight at once);
+//   POPC   popcount brute force: number of database splits (grid depth);
+//   TC     tensor-core brute force: number of database splits (work units
+//          per persistent CTA).
+// dt_autotune times each candidate on the caller's data with CUDA events
+// and keeps the fastest per key (kind, log2 n, log2 nq, k, SM count) in a
+// process-wide table; launchers look the key up and fall back to their
+// built-in heuristics.  The table can be saved to and loaded from a text
+// file (one "kind n_log nq_log k sms a b" line per entry).
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "dt_internal.cuh"
+
+namespace dtk {
+namespace {
+
+using Key = std::tuple<int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<Key, TuneCfg> g_tune;
+
+int log2i(int64_t v)
+{
+    int r = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+Key make_key(TuneKind kind, int64_t n, int64_t nq, int k)
+{
+    return Key((int)kind, log2i(n), log2i(nq), k, sm_count());
+}
+
+}  // namespace
+
+bool tune_lookup(TuneKind kind, int64_t n, int64_t nq, int k, TuneCfg *cfg)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(make_key(kind, n, nq, k));
+    if (it == g_tune.end()) return false;
+    *cfg = it->second;
+    return true;
+}
+
+void tune_store(TuneKind kind, int64_t n, int64_t nq, int k, const TuneCfg &cfg)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[make_key(kind, n, nq, k)] = cfg;
+}
+
+void tune_clear()
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.clear();
+}
+
+namespace {
+
+// Time fn() once after one warm-up; milliseconds, or -1 on failure.
+template <typename F>
+float time_call(F fn, cudaStream_t s)
+{
+    if (fn() != DT_OK) return -1.f;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return -1.f;
+    }
+    cudaEventRecord(a, s);
+    int rc = fn();
+    cudaEventRecord(b, s);
+    float ms = -1.f;
+    if (rc == DT_OK && cudaEventSynchronize(b) == cudaSuccess) cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+}  // namespace
+}  // namespace dtk
+
+using namespace dtk;
+
+extern "C" {
+
+int dt_autotune(const dt_index *ix, const uint64_t *d_db, int64_t n, const uint64_t *d_q,
+                int64_t nq, int32_t k, void *stream, dt_tune_report *report)
+{
+    if (report) *report = dt_tune_report{};
+    DT_CHECK_ARG(d_q != nullptr && nq >= 1, "queries required");
+    DT_CHECK_ARG(k >= 1 && k <= DT_MAX_K, "k must be in [1, DT_MAX_K]");
+    DT_CHECK_ARG(ix != nullptr || (d_db != nullptr && n >= 1), "an index or a database is required");
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *idx = nullptr;
+    float *score = nullptr;
+    DT_CUDA_TRY(cudaMallocAsync((void **)&idx, (size_t)nq * k * 4, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&score, (size_t)nq * k * 4, s));
+    int tried = 0;
+    if (ix) {
+        TuneCfg best{0, 0};
+        float best_ms = 1e30f;
+        for (int threads : {128, 256})
+            for (int bps : {1, 2, 3, 4, 6, 8}) {
+                if (threads * bps > 2048) continue;
+                TuneCfg c{threads, bps};
+                float ms = time_call([&] {
+                    return launch_dt_search_cfg(ix, d_q, nq, k, idx, score, nullptr, nullptr, s, &c);
+                }, s);
+                ++tried;
+                if (ms > 0.f && ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+        if (best.a) {
+            tune_store(TUNE_TREE, ix->n, nq, k, best);
+            if (report) {
+                report->tree_threads = best.a;
+                report->tree_blocks_per_sm = best.b;
+                report->tree_ms = best_ms;
+            }
+        }
+    }
+    if (d_db) {
+        for (int kind = TUNE_POPC; kind <= TUNE_TC; ++kind) {
+            TuneCfg best{0, 0};
+            float best_ms = 1e30f;
+            for (int splits : {1, 2, 4, 8, 16, 32, 64, 128}) {
+                TuneCfg c{splits, 0};
+                float ms = time_call([&] {
+                    return kind == TUNE_POPC
+                               ? launch_bf_popc_cfg(d_db, n, d_q, nq, k, idx, score, nullptr, s, &c)
+                               : launch_bf_tc_cfg(d_db, n, d_q, nq, k, idx, score, nullptr, s, &c);
+                }, s);
+                ++tried;
+                if (ms > 0.f && ms < best_ms) {
+                    best_ms = ms;
+                    best = c;
+                }
+            }
+            if (best.a) {
+                tune_store((TuneKind)kind, n, nq, k, best);
+                if (report) {
+                    if (kind == TUNE_POPC) {
+                        report->popc_splits = best.a;
+                        report->popc_ms = best_ms;
+                    } else {
+                        report->tc_splits = best.a;
+                        report->tc_ms = best_ms;
+                    }
+                }
+            }
+        }
+    }
+    cudaFreeAsync(score, s);
+    cudaFreeAsync(idx, s);
+    DT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (report) report->candidates_timed = tried;
+    return DT_OK;
+}
+
+int dt_tune_save(const char *path)
+{
+    DT_CHECK_ARG(path != nullptr, "path must not be NULL");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE *f = std::fopen(path, "w");
+    DT_CHECK_ARG(f != nullptr, "cannot open the tuning file for writing");
+    for (const auto &e : g_tune)
+        std::fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(e.first), std::get<1>(e.first),
+                     std::get<2>(e.first), std::get<3>(e.first), std::get<4>(e.first), e.second.a,
+                     e.second.b);
+    std::fclose(f);
+    return DT_OK;
+}
+
+int dt_tune_load(const char *path)
+{
+    DT_CHECK_ARG(path != nullptr, "path must not be NULL");
+    FILE *f = std::fopen(path, "r");
+    DT_CHECK_ARG(f != nullptr, "cannot open the tuning file");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    int kind, nl, ql, k, sms, a, b, loaded = 0;
+    while (std::fscanf(f, "%d %d %d %d %d %d %d", &kind, &nl, &ql, &k, &sms, &a, &b) == 7) {
+        if (kind < TUNE_TREE || kind > TUNE_TC || a <= 0 || b < 0) continue;
+        g_tune[Key(kind, nl, ql, k, sms)] = TuneCfg{a, b};
+        ++loaded;
+    }
+    std::fclose(f);
+    return loaded;
+}
+
+void dt_tune_clear(void) { tune_clear(); }
+
+}  // extern "C"

@@ -287,6 +287,13 @@ int take_bf_error(bool *raised)
 int launch_bf_popc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                    uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s)
 {
+    return launch_bf_popc_cfg(db, n, q, nq, k, idx, score, ab, s, nullptr);
+}
+
+int launch_bf_popc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                       uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s,
+                       const TuneCfg *cfg)
+{
     const size_t smem = sizeof(BfSmem) + (size_t)QB * k * sizeof(uint64_t);
     static bool attr_set = false;
     if (!attr_set) {
@@ -299,7 +306,10 @@ int launch_bf_popc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq,
     int per_sm = 0;
     DT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bf_popc_kernel, THREADS, smem));
     const int concurrent = std::max(1, per_sm) * sm_count();
-    const int splits = pick_splits(qblocks, tiles, concurrent);
+    TuneCfg c{0, 0};
+    if (cfg) c = *cfg;
+    else tune_lookup(TUNE_POPC, n, nq, k, &c);
+    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, tiles) : pick_splits(qblocks, tiles, concurrent);
     const int64_t tiles_per_split = (tiles + splits - 1) / splits;
     const int n_split = (int)((tiles + tiles_per_split - 1) / tiles_per_split);
 

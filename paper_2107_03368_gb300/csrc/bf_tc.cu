@@ -422,7 +422,8 @@ __global__ void merge_top1_kernel(const uint64_t *__restrict__ partial, int n_sp
 // Per-split top-k lists of every query over db (rows reported through
 // idx_map when given).  *partial is allocated on the stream; the caller frees it.
 int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
-                    int64_t nq, int k, cudaStream_t s, uint64_t **partial_out, int *n_split_out)
+                    int64_t nq, int k, cudaStream_t s, uint64_t **partial_out, int *n_split_out,
+                    const TuneCfg *cfg)
 {
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
@@ -434,7 +435,11 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     const int n_mtiles = (int)((nq + TM - 1) / TM);
     const int64_t n_ntiles = (n + TN - 1) / TN;
     const int sms = sm_count();
-    const int splits = pick_bf_splits(n_mtiles, n_ntiles, sms);
+    TuneCfg c{0, 0};
+    if (cfg) c = *cfg;
+    else tune_lookup(TUNE_TC, n, nq, k, &c);
+    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_ntiles)
+                               : pick_bf_splits(n_mtiles, n_ntiles, sms);
     const int64_t tiles_per_split = (n_ntiles + splits - 1) / splits;
     const int n_split = (int)((n_ntiles + tiles_per_split - 1) / tiles_per_split);
     const int64_t units = (int64_t)n_mtiles * n_split;
@@ -485,12 +490,23 @@ int take_tc_error(bool *raised)
     return DT_OK;
 }
 
+int launch_bf_tc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                     uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s, const TuneCfg *cfg)
+{
+    uint64_t *partial = nullptr;
+    int n_split = 0;
+    if (int r = tc_partial_topk(db, n, nullptr, q, nq, k, s, &partial, &n_split, cfg)) return r;
+    int rc = launch_merge_partials(partial, n_split, db, q, nq, k, idx, score, ab, s);
+    cudaFreeAsync(partial, s);
+    return rc;
+}
+
 int launch_bf_tc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                  uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s)
 {
     uint64_t *partial = nullptr;
     int n_split = 0;
-    if (int r = tc_partial_topk(db, n, nullptr, q, nq, k, s, &partial, &n_split)) return r;
+    if (int r = tc_partial_topk(db, n, nullptr, q, nq, k, s, &partial, &n_split, nullptr)) return r;
     int rc = launch_merge_partials(partial, n_split, db, q, nq, k, idx, score, ab, s);
     cudaFreeAsync(partial, s);
     return rc;
@@ -501,7 +517,7 @@ int launch_tc_top1(const uint64_t *db, int64_t n, const uint32_t *idx_map, const
 {
     uint64_t *partial = nullptr;
     int n_split = 0;
-    if (int r = tc_partial_topk(db, n, idx_map, q, nq, 1, s, &partial, &n_split)) return r;
+    if (int r = tc_partial_topk(db, n, idx_map, q, nq, 1, s, &partial, &n_split, nullptr)) return r;
     merge_top1_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(partial, n_split, nq, nn);
     DT_CUDA_TRY(cudaGetLastError());
     cudaFreeAsync(partial, s);

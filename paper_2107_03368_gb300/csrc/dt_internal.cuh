@@ -157,7 +157,26 @@ struct dt_index {
 };
 
 namespace dtk {
+// Autotuner table (autotune.cu): a launch shape per kernel kind and problem size.
+enum TuneKind { TUNE_TREE = 0, TUNE_POPC = 1, TUNE_TC = 2 };
+struct TuneCfg {
+    int a;   // TREE: threads per block; POPC / TC: database splits
+    int b;   // TREE: resident blocks per SM
+};
+bool tune_lookup(TuneKind kind, int64_t n, int64_t nq, int k, TuneCfg *cfg);
+void tune_store(TuneKind kind, int64_t n, int64_t nq, int k, const TuneCfg &cfg);
+
 // Launchers implemented in the kernel files (stream-ordered, no sync unless noted).
+// The *_cfg variants take an explicit launch shape (NULL: table or heuristic).
+int launch_dt_search_cfg(const dt_index *ix, const uint64_t *q, int64_t nq, int k, uint32_t *idx,
+                         float *score, uint16_t *ab, dt_stats *stats, cudaStream_t s,
+                         const TuneCfg *cfg);
+int launch_bf_popc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                       uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s,
+                       const TuneCfg *cfg);
+int launch_bf_tc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
+                     uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s,
+                     const TuneCfg *cfg);
 int pick_bf_splits(int64_t row_blocks, int64_t tiles, int concurrent);
 // Merge per-split sorted top-k lists partial[split][q][k] into idx/score/(A,B).
 int launch_merge_partials(const uint64_t *partial, int n_split, const uint64_t *db,

@@ -9,7 +9,6 @@
 namespace dtk {
 namespace {
 
-constexpr int ST = 256;   // threads per CTA (8 warps)
 
 struct SearchCtl {
     unsigned long long next;      // next query to hand out
@@ -17,8 +16,8 @@ struct SearchCtl {
     unsigned int error;           // 1 = stack overflow
 };
 
-template <bool USE_AND>
-__global__ void __launch_bounds__(ST)
+template <bool USE_AND, int NT>
+__global__ void __launch_bounds__(NT)
 dt_search_kernel(TreeView tv, const uint32_t *__restrict__ iperm, const uint64_t *__restrict__ qs,
                  int64_t nq, int k, uint64_t *__restrict__ stacks, int stack_cap,
                  SearchCtl *ctl, uint32_t *__restrict__ idx, float *__restrict__ score,
@@ -75,26 +74,33 @@ dt_search_kernel(TreeView tv, const uint32_t *__restrict__ iperm, const uint64_t
 
 }  // namespace
 
-int launch_dt_search(const dt_index *ix, const uint64_t *q, int64_t nq, int k, uint32_t *idx,
-                     float *score, uint16_t *ab, dt_stats *stats, cudaStream_t s)
+int launch_dt_search_cfg(const dt_index *ix, const uint64_t *q, int64_t nq, int k, uint32_t *idx,
+                         float *score, uint16_t *ab, dt_stats *stats, cudaStream_t s,
+                         const TuneCfg *cfg)
 {
     TreeView tv{ix->node, ix->or_img, ix->and_img, ix->db_tree, ix->perm};
-    auto kern = ix->use_and ? dt_search_kernel<true> : dt_search_kernel<false>;
+    TuneCfg c{256, 0};
+    if (cfg) c = *cfg;
+    else tune_lookup(TUNE_TREE, ix->n, nq, k, &c);
+    const int nt = c.a == 128 ? 128 : 256;
+    auto kern = ix->use_and ? (nt == 128 ? dt_search_kernel<true, 128> : dt_search_kernel<true, 256>)
+                            : (nt == 128 ? dt_search_kernel<false, 128> : dt_search_kernel<false, 256>);
     int per_sm = 0;
-    DT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ST, 0));
-    const int64_t warps_needed = nq;
-    int64_t blocks = std::max(1, per_sm) * (int64_t)sm_count();
-    blocks = std::min<int64_t>(blocks, (warps_needed + ST / 32 - 1) / (ST / 32));
+    DT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, 0));
+    per_sm = std::max(1, per_sm);
+    if (c.b > 0) per_sm = std::min(per_sm, c.b);   // fewer queries in flight than fit
+    int64_t blocks = per_sm * (int64_t)sm_count();
+    blocks = std::min<int64_t>(blocks, (nq + nt / 32 - 1) / (nt / 32));
     blocks = std::max<int64_t>(blocks, 1);
     const int stack_cap = ix->depth + 2;
-    const int64_t nwarps = blocks * (ST / 32);
+    const int64_t nwarps = blocks * (nt / 32);
 
     SearchCtl *ctl = nullptr;
     uint64_t *stacks = nullptr;
     DT_CUDA_TRY(cudaMallocAsync((void **)&ctl, sizeof(SearchCtl), s));
     DT_CUDA_TRY(cudaMallocAsync((void **)&stacks, (size_t)nwarps * stack_cap * 8, s));
     DT_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(SearchCtl), s));
-    kern<<<(unsigned)blocks, ST, 0, s>>>(tv, ix->iperm, q, nq, k, stacks, stack_cap, ctl, idx,
+    kern<<<(unsigned)blocks, nt, 0, s>>>(tv, ix->iperm, q, nq, k, stacks, stack_cap, ctl, idx,
                                          score, ab);
     DT_CUDA_TRY(cudaGetLastError());
     int rc = DT_OK;
@@ -114,6 +120,12 @@ int launch_dt_search(const dt_index *ix, const uint64_t *q, int64_t nq, int k, u
     DT_CUDA_TRY(cudaFreeAsync(stacks, s));
     DT_CUDA_TRY(cudaFreeAsync(ctl, s));
     return rc;
+}
+
+int launch_dt_search(const dt_index *ix, const uint64_t *q, int64_t nq, int k, uint32_t *idx,
+                     float *score, uint16_t *ab, dt_stats *stats, cudaStream_t s)
+{
+    return launch_dt_search_cfg(ix, q, nq, k, idx, score, ab, stats, s, nullptr);
 }
 
 }  // namespace dtk

@@ -48,6 +48,16 @@ class IndexInfo(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("tree_threads", ctypes.c_int32), ("tree_blocks_per_sm", ctypes.c_int32),
+                ("popc_splits", ctypes.c_int32), ("tc_splits", ctypes.c_int32),
+                ("tree_ms", ctypes.c_float), ("popc_ms", ctypes.c_float), ("tc_ms", ctypes.c_float),
+                ("candidates_timed", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("nodes_visited", ctypes.c_int64), ("leaves_visited", ctypes.c_int64),
                 ("descs_scanned", ctypes.c_int64), ("bounds_evaluated", ctypes.c_int64)]
@@ -72,6 +82,10 @@ def load():
             "retrieve_objects": ([P, P, i32, P, P, i32, i64, i32, u64, P, P, P, i32, P],
                                  ctypes.c_int),
             "dt_sync_status": ([P], ctypes.c_int),
+            "dt_autotune": ([P, P, i64, P, i64, i32, P, P], ctypes.c_int),
+            "dt_tune_save": ([ctypes.c_char_p], ctypes.c_int),
+            "dt_tune_load": ([ctypes.c_char_p], ctypes.c_int),
+            "dt_tune_clear": ([], None),
             "dt_free": ([P], None),
             "dt_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "dt_last_error": ([], ctypes.c_char_p),
@@ -226,6 +240,33 @@ def retrieve_objects(index: Index, object_of, n_objects, qdesc, qoffsets, vote_t
                                    _ptr(consumed), engine, _stream(stream)),
            "retrieve_objects")
     return votes, winner, consumed
+
+
+def dt_autotune(index=None, db=None, q=None, k=10, stream=None):
+    """Time launch shapes on these inputs and remember the fastest (returns the report)."""
+    q = _desc(q, "q")
+    if db is not None:
+        db = _desc(db, "db")
+    rep = TuneReport()
+    _check(load().dt_autotune(index.handle if index is not None else None, _ptr(db),
+                              db.shape[0] if db is not None else 0, _ptr(q), q.shape[0], k,
+                              _stream(stream), ctypes.byref(rep)), "dt_autotune")
+    return rep.as_dict()
+
+
+def dt_tune_save(path):
+    _check(load().dt_tune_save(str(path).encode()), "dt_tune_save")
+
+
+def dt_tune_load(path):
+    n = load().dt_tune_load(str(path).encode())
+    if n < 0:
+        raise DtError(n, "dt_tune_load")
+    return n
+
+
+def dt_tune_clear():
+    load().dt_tune_clear()
 
 
 def dt_sync_status(stream=None):

@@ -57,3 +57,16 @@ def test_bad_sizes_are_rejected():
     assert lib.retrieve_objects(None, None, 3, None, None, 1, 10, 0, 0, None, None, None, 0,
                                 None) == dt.DT_EINVAL
     assert lib.dt_get_info(None, None) == dt.DT_EINVAL
+
+
+def test_tune_table_file_roundtrip(tmp_path):
+    p = tmp_path / "tune.txt"
+    p.write_text("0 23 13 10 152 256 3\n1 23 13 10 152 8 0\nbad line\n")
+    dt.dt_tune_clear()
+    assert dt.dt_tune_load(p) == 2
+    out = tmp_path / "out.txt"
+    dt.dt_tune_save(out)
+    assert sorted(out.read_text().split("\n")[:2]) == ["0 23 13 10 152 256 3", "1 23 13 10 152 8 0"]
+    dt.dt_tune_clear()
+    with pytest.raises(dt.DtError):
+        dt.dt_tune_load(tmp_path / "missing.txt")
