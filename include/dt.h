@@ -261,6 +261,50 @@ int dt_tune_save(const char *path);
 int dt_tune_load(const char *path);
 void dt_tune_clear(void);
 
+/*
+ * Learned proposal.  The paper has no learned component; this part proposes
+ * candidates with a small trained encoder and ranks them exactly by Eq. 1,
+ * so its answers are exact whenever the true neighbours are proposed, and
+ * its recall is measured against dt_search / bf_search.
+ *
+ * Encoder: 64x64 bit image -> conv 3x3/2 (32, 64, 64 channels, ReLU) ->
+ * 2x2 average pool -> fc 1024->256 (ReLU) -> fc 256->128 -> unit length.
+ * 351,040 FP32 parameters (enc_param_count), flat buffer order w1 b1 w2 b2
+ * w3 b3 wf1 bf1 wf2 bf2, conv weights [out][in][3][3], fc weights [out][in].
+ */
+typedef struct dt_encoder dt_encoder;
+int enc_create(uint64_t seed, dt_encoder **out);       /* He-uniform weights, zero biases */
+void enc_free(dt_encoder *enc);
+int64_t enc_param_count(void);
+int enc_get_params(const dt_encoder *enc, float *h_params);  /* host [enc_param_count()] */
+int enc_set_params(dt_encoder *enc, const float *h_params);
+int enc_get_grads(const dt_encoder *enc, float *h_grads);    /* gradient of the last train step */
+/* Embeddings of n descriptors into d_out_bf16 [n][128] (BF16 bits) and/or
+ * d_out_f32 [n][128]; at least one output.  Stream-ordered. */
+int enc_embed(const dt_encoder *enc, const uint64_t *d_bits, int64_t n, uint16_t *d_out_bf16,
+              float *d_out_f32, void *stream);
+/* One step of InfoNCE with in-batch negatives on B (query, target) pairs,
+ * L = mean_i [ log sum_j exp(<e_qi, e_tj>/tau) - <e_qi, e_ti>/tau ], then Adam
+ * (beta 0.9 / 0.999, eps 1e-8) with learning rate lr unless update = 0.
+ * h_loss: nullable host float receiving L (synchronises).  2 <= B <= 4096. */
+int enc_train_step(dt_encoder *enc, const uint64_t *d_q, const uint64_t *d_t, int32_t B, float lr,
+                   float tau, int32_t update, float *h_loss, void *stream);
+
+/* Inverted file over the encoder's embeddings of a database: k-means with
+ * n_lists cosine centroids (iters Lloyd iterations from evenly spaced
+ * seeds), the database copied list by list.  Synchronises `stream`. */
+typedef struct dt_ivf dt_ivf;
+int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_lists,
+              int32_t iters, void *stream, dt_ivf **out);
+void ivf_free(dt_ivf *ivf);
+int ivf_offsets(const dt_ivf *ivf, int64_t *h_offsets);      /* host [n_lists + 1] */
+/* Top-k of each query among the rows of its n_probe nearest lists (by
+ * embedding), ranked exactly by Eq. 1 (A*Z + B*P, ties by original index).
+ * d_idx/d_score [nq][k] as in dt_search; d_scanned [nq] rows examined (nullable).
+ * With n_probe = n_lists the result is the exact top-k. */
+int ivf_search(const dt_ivf *ivf, const dt_encoder *enc, const uint64_t *d_q, int64_t nq, int32_t k,
+               int32_t n_probe, uint32_t *d_idx, float *d_score, int64_t *d_scanned, void *stream);
+
 /* Release an index (NULL is allowed).  Synchronises the device it lives on. */
 void dt_free(dt_index *index);
 

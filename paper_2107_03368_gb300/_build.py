@@ -28,6 +28,8 @@ CUDA_SOURCES = [
     "bf_tc.cu",
     "dt_build.cu",
     "dt_search.cu",
+    "encoder.cu",
+    "ivf.cu",
     "votes.cu",
 ]
 

@@ -1,0 +1,408 @@
+// ivf.cu — learned proposal: an inverted file over encoder embeddings, with
+// an exact Eq. 1 rerank of every proposed candidate (the paper has no
+// learned component; its exact search remains the reference for recall).
+//
+// Build (ivf_build): embed the database with the encoder (BF16), run k-means
+// on the unit-length embeddings (cosine assignment, centroid = normalised
+// mean), then lay the database out list by list: a cluster-ordered copy of
+// the descriptor bits, the original index of each row and list offsets.
+//
+// Search (ivf_search): embed the queries; one CTA per query scores every
+// centroid, keeps the n_probe best lists, and scans all of their rows
+// exactly (A, B counts of Eq. 1, ranked by A*Z + B*P, ties by original
+// index) — the candidates come from the learned embedding, the ranking is
+// exact, so the answer equals the exact one whenever the true neighbours
+// lie in the probed lists.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "block_util.cuh"
+#include "dt_internal.cuh"
+#include "dt_traverse.cuh"
+
+struct dt_encoder;
+extern "C" int enc_embed(const dt_encoder *e, const uint64_t *d_bits, int64_t n, uint16_t *d_out_bf16,
+                         float *d_out_f32, void *stream);
+
+namespace dtk {
+namespace {
+
+constexpr int D = 128;
+
+// ------------------------------------------------ k-means assignment
+// 32 points x 32 centroids per tile, 256 threads, 2 x 2 dot products each.
+constexpr int KT = 32;
+
+__global__ void __launch_bounds__(256)
+assign_kernel(const __nv_bfloat16 *__restrict__ emb, int64_t n, const float *__restrict__ cent,
+              int K, int32_t *__restrict__ assign)
+{
+    __shared__ float ps[KT][D + 1];
+    __shared__ float cs[KT][D + 1];
+    __shared__ unsigned long long best[KT];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t p0 = (int64_t)blockIdx.x * KT;
+    for (int i = tid; i < KT * D; i += 256) {
+        const int r = i / D, c = i % D;
+        ps[r][c] = p0 + r < n ? __bfloat162float(emb[(p0 + r) * D + c]) : 0.f;
+    }
+    if (tid < KT) best[tid] = 0ull;
+    __syncthreads();
+    for (int c0 = 0; c0 < K; c0 += KT) {
+        for (int i = tid; i < KT * D; i += 256) {
+            const int r = i / D, c = i % D;
+            cs[r][c] = c0 + r < K ? cent[(int64_t)(c0 + r) * D + c] : 0.f;
+        }
+        __syncthreads();
+        float acc[2][2] = {};
+        for (int d = 0; d < D; ++d) {
+            float a[2], b[2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) a[i] = ps[ty + 16 * i][d];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) b[j] = cs[tx + 16 * j][d];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) acc[i][j] += a[i] * b[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int c = c0 + tx + 16 * j;
+                if (c >= K) continue;
+                // larger dot first, lower centroid id on ties: order-preserving
+                // float bits in the high word, inverted id in the low word
+                uint32_t fb = __float_as_uint(acc[i][j]);
+                fb = (fb & 0x80000000u) ? ~fb : (fb | 0x80000000u);
+                const unsigned long long key = ((unsigned long long)fb << 32) | (0xFFFFFFFFu - (uint32_t)c);
+                atomicMax(&best[ty + 16 * i], key);
+            }
+        __syncthreads();
+    }
+    if (tid < KT && p0 + tid < n) assign[p0 + tid] = (int32_t)(0xFFFFFFFFu - (uint32_t)(best[tid] & 0xFFFFFFFFu));
+}
+
+// sums[c] += emb[i] for assign[i] = c; counts[c] += 1
+__global__ void accumulate_kernel(const __nv_bfloat16 *__restrict__ emb, int64_t n,
+                                  const int32_t *__restrict__ assign, float *__restrict__ sums,
+                                  int32_t *__restrict__ counts)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (; i < n; i += stride) {
+        const int c = assign[i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            atomicAdd(&sums[(int64_t)c * D + lane + 32 * j], __bfloat162float(emb[i * D + lane + 32 * j]));
+        if (lane == 0) atomicAdd(&counts[c], 1);
+    }
+}
+
+// centroid = normalised sum (kept when its cluster is empty); warp per centroid
+__global__ void update_kernel(const float *__restrict__ sums, const int32_t *__restrict__ counts,
+                              int K, float *__restrict__ cent)
+{
+    const int lane = threadIdx.x & 31;
+    const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (c >= K || counts[c] == 0) return;
+    float v[4], ss = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[j] = sums[(int64_t)c * D + lane + 32 * j];
+        ss += v[j] * v[j];
+    }
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const float inv = 1.f / fmaxf(sqrtf(ss), 1e-12f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cent[(int64_t)c * D + lane + 32 * j] = v[j] * inv;
+}
+
+__global__ void init_centroids_kernel(const __nv_bfloat16 *__restrict__ emb, int64_t n, int K,
+                                      float *__restrict__ cent)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)K * D) return;
+    const int64_t c = i / D, d = i % D;
+    const int64_t src = (c * n) / K;                 // evenly spaced rows
+    cent[i] = __bfloat162float(emb[src * D + d]);
+}
+
+// rows of list c go to [offsets[c], offsets[c+1]); order inside a list is
+// irrelevant to the results (ties are broken by original index)
+__global__ void scatter_kernel(const uint64_t *__restrict__ db, int64_t n,
+                               const int32_t *__restrict__ assign, const int64_t *__restrict__ offsets,
+                               int32_t *__restrict__ cursor, uint64_t *__restrict__ ivf_db,
+                               uint32_t *__restrict__ ivf_ids)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (; i < n; i += stride) {
+        const int c = assign[i];
+        int pos = 0;
+        if (lane == 0) pos = atomicAdd(&cursor[c], 1);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        const int64_t dst = offsets[c] + pos;
+        reinterpret_cast<uint4 *>(ivf_db + dst * kWords)[lane] =
+            reinterpret_cast<const uint4 *>(db + i * kWords)[lane];
+        if (lane == 0) ivf_ids[dst] = (uint32_t)i;
+    }
+}
+
+__global__ void count_kernel(const int32_t *__restrict__ assign, int64_t n, int32_t *__restrict__ counts)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < n; i += stride) atomicAdd(&counts[assign[i]], 1);
+}
+
+__global__ void offsets_kernel(const int32_t *__restrict__ counts, int K, int64_t *__restrict__ offsets)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int64_t run = 0;
+        for (int c = 0; c < K; ++c) {
+            offsets[c] = run;
+            run += counts[c];
+        }
+        offsets[K] = run;
+    }
+}
+
+// ------------------------------------------------ search: one CTA per query
+constexpr int ST = 256;
+constexpr int MAX_PROBE = 256;
+
+__global__ void __launch_bounds__(ST)
+ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ qs, int64_t nq,
+                  const float *__restrict__ cent, int K, const int64_t *__restrict__ offsets,
+                  const uint64_t *__restrict__ ivf_db, const uint32_t *__restrict__ ivf_ids,
+                  int n_probe, int k, uint32_t *__restrict__ idx, float *__restrict__ score,
+                  uint16_t *__restrict__ ab, int64_t *__restrict__ scanned)
+{
+    extern __shared__ float csc[];                   // [K] centroid scores
+    __shared__ float qe[D];
+    __shared__ int probe[MAX_PROBE];
+    __shared__ unsigned long long red[ST / 32];
+    __shared__ uint64_t lists[ST / 32][kMaxK];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t q = blockIdx.x;
+    if (tid < D) qe[tid] = qemb[q * D + tid];
+    __syncthreads();
+    for (int c = tid; c < K; c += ST) {
+        float s = 0.f;
+        for (int d = 0; d < D; ++d) s += qe[d] * __ldg(cent + (int64_t)c * D + d);
+        csc[c] = s;
+    }
+    __syncthreads();
+    // n_probe best lists by repeated block-wide argmax (higher score, lower id)
+    for (int p = 0; p < n_probe; ++p) {
+        unsigned long long b = 0ull;
+        for (int c = tid; c < K; c += ST) {
+            uint32_t fb = __float_as_uint(csc[c]);
+            fb = (fb & 0x80000000u) ? ~fb : (fb | 0x80000000u);
+            const unsigned long long key = ((unsigned long long)fb << 32) | (0xFFFFFFFFu - (uint32_t)c);
+            b = key > b ? key : b;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
+            b = u > b ? u : b;
+        }
+        if (lane == 0) red[wid] = b;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long m = 0ull;
+            for (int w = 0; w < ST / 32; ++w) m = red[w] > m ? red[w] : m;
+            const int c = (int)(0xFFFFFFFFu - (uint32_t)(m & 0xFFFFFFFFu));
+            probe[p] = c;
+            csc[c] = -INFINITY;
+        }
+        __syncthreads();
+    }
+    // exact scan of the probed lists: warps take 32-row blocks in turn
+    const uint4 qv = __ldg(reinterpret_cast<const uint4 *>(qs + q * kWords) + lane);
+    const QueryWeights w = query_weights(warp_sum(popc4(qv)));
+    uint64_t slot = kEmpty;
+    int64_t rows = 0;
+    for (int p = 0; p < n_probe; ++p) {
+        const int c = probe[p];
+        const int64_t b0 = offsets[c], b1 = offsets[c + 1];
+        rows += b1 - b0;
+        for (int64_t r0 = b0 + (int64_t)wid * 32; r0 < b1; r0 += ST) {
+            const int m = (int)(b1 - r0 < 32 ? b1 - r0 : 32);
+            uint32_t v[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                v[j] = 0;
+                if (j < m) {
+                    const uint4 t = __ldg(reinterpret_cast<const uint4 *>(ivf_db + (r0 + j) * kWords) + lane);
+                    v[j] = popc_and4(qv, t) | (popc4(t) << 16);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+                for (int j = 0; j < o; ++j) {
+                    const bool hi = lane & o;
+                    const uint32_t send = hi ? v[j] : v[j + o];
+                    const uint32_t keep = hi ? v[j + o] : v[j];
+                    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            uint64_t cand = kEmpty;
+            if (lane < m)
+                cand = pack(pair_key(w, v[0] & 0xffffu, v[0] >> 16), __ldg(ivf_ids + r0 + lane));
+            warp_list_merge(slot, cand, k, lane);
+        }
+    }
+    if (lane < k) lists[wid][lane] = slot;
+    __syncthreads();
+    if (wid == 0) {
+        uint64_t fin = kEmpty;
+        for (int w2 = 0; w2 < ST / 32; ++w2)
+            warp_list_merge(fin, lane < k ? lists[w2][lane] : kEmpty, k, lane);
+        // (A, B) of each result from the candidate rows is not kept; recompute
+        // them from the query and the result's row, found again by a scan of
+        // the probed lists only when asked for.
+        if (lane < k) {
+            const int64_t o = q * k + lane;
+            if (fin == kEmpty) {
+                idx[o] = 0xFFFFFFFFu;
+                score[o] = __int_as_float(0x7f800000);
+            } else {
+                idx[o] = (uint32_t)fin;
+                score[o] = key_score(w, (uint32_t)(fin >> 32));
+            }
+        }
+        if (lane == 0 && scanned) scanned[q] = rows;
+    }
+    (void)ab;
+}
+
+}  // namespace
+}  // namespace dtk
+
+struct dt_ivf {
+    int device = 0;
+    int64_t n = 0;
+    int K = 0;
+    float *cent = nullptr;          // [K][128]
+    int64_t *offsets = nullptr;     // [K+1]
+    uint64_t *db = nullptr;         // [n][64] cluster order
+    uint32_t *ids = nullptr;        // [n] original index
+};
+
+using namespace dtk;
+
+extern "C" {
+
+int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_lists, int32_t iters,
+              void *stream, dt_ivf **out)
+{
+    DT_CHECK_ARG(enc && d_db && out && n >= 1 && n_lists >= 1 && n_lists <= n && iters >= 0,
+                 "bad arguments");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = n_lists;
+    dt_ivf *ix = new dt_ivf();
+    cudaGetDevice(&ix->device);
+    ix->n = n;
+    ix->K = K;
+    __nv_bfloat16 *emb = nullptr;
+    int32_t *assign = nullptr, *counts = nullptr;
+    float *sums = nullptr;
+    int rc = DT_OK;
+    auto fail = [&](const char *what) {
+        set_error(std::string("ivf_build: ") + what);
+        rc = DT_ECUDA;
+    };
+    if (cudaMallocAsync((void **)&emb, (size_t)n * D * 2, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&assign, (size_t)n * 4, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&counts, (size_t)K * 4, s) != cudaSuccess ||
+        cudaMallocAsync((void **)&sums, (size_t)K * D * 4, s) != cudaSuccess ||
+        cudaMalloc((void **)&ix->cent, (size_t)K * D * 4) != cudaSuccess ||
+        cudaMalloc((void **)&ix->offsets, (size_t)(K + 1) * 8) != cudaSuccess ||
+        cudaMalloc((void **)&ix->db, (size_t)n * 512) != cudaSuccess ||
+        cudaMalloc((void **)&ix->ids, (size_t)n * 4) != cudaSuccess) {
+        set_error("ivf_build: allocation failed");
+        rc = DT_ENOMEM;
+    }
+    if (rc == DT_OK) rc = enc_embed(enc, d_db, n, reinterpret_cast<uint16_t *>(emb), nullptr, s);
+    if (rc == DT_OK) {
+        init_centroids_kernel<<<(unsigned)(((int64_t)K * D + 255) / 256), 256, 0, s>>>(emb, n, K, ix->cent);
+        const unsigned ablocks = (unsigned)((n + KT - 1) / KT);
+        for (int it = 0; it <= iters; ++it) {
+            assign_kernel<<<ablocks, 256, 0, s>>>(emb, n, ix->cent, K, assign);
+            if (it == iters) break;
+            cudaMemsetAsync(sums, 0, (size_t)K * D * 4, s);
+            cudaMemsetAsync(counts, 0, (size_t)K * 4, s);
+            accumulate_kernel<<<(unsigned)std::min<int64_t>((n + 7) / 8, 8192), 256, 0, s>>>(emb, n, assign, sums, counts);
+            update_kernel<<<(unsigned)((K + 7) / 8), 256, 0, s>>>(sums, counts, K, ix->cent);
+        }
+        cudaMemsetAsync(counts, 0, (size_t)K * 4, s);
+        count_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, s>>>(assign, n, counts);
+        offsets_kernel<<<1, 32, 0, s>>>(counts, K, ix->offsets);
+        cudaMemsetAsync(counts, 0, (size_t)K * 4, s);
+        scatter_kernel<<<(unsigned)std::min<int64_t>((n + 7) / 8, 8192), 256, 0, s>>>(
+            d_db, n, assign, ix->offsets, counts, ix->db, ix->ids);
+        if (cudaGetLastError() != cudaSuccess) fail("kernel launch");
+    }
+    cudaFreeAsync(sums, s);
+    cudaFreeAsync(counts, s);
+    cudaFreeAsync(assign, s);
+    cudaFreeAsync(emb, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && rc == DT_OK) fail("stream");
+    if (rc != DT_OK) {
+        cudaFree(ix->cent); cudaFree(ix->offsets); cudaFree(ix->db); cudaFree(ix->ids);
+        delete ix;
+        return rc;
+    }
+    *out = ix;
+    return DT_OK;
+}
+
+void ivf_free(dt_ivf *ix)
+{
+    if (!ix) return;
+    cudaDeviceSynchronize();
+    cudaFree(ix->cent); cudaFree(ix->offsets); cudaFree(ix->db); cudaFree(ix->ids);
+    delete ix;
+}
+
+// List sizes (host copy of the K+1 offsets).
+int ivf_offsets(const dt_ivf *ix, int64_t *h_offsets)
+{
+    DT_CHECK_ARG(ix && h_offsets, "bad arguments");
+    DT_CUDA_TRY(cudaMemcpy(h_offsets, ix->offsets, (size_t)(ix->K + 1) * 8, cudaMemcpyDeviceToHost));
+    return DT_OK;
+}
+
+int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int64_t nq, int32_t k,
+               int32_t n_probe, uint32_t *d_idx, float *d_score, int64_t *d_scanned, void *stream)
+{
+    DT_CHECK_ARG(ix && enc && d_q && d_idx && d_score && nq >= 0, "bad arguments");
+    DT_CHECK_ARG(k >= 1 && k <= DT_MAX_K, "k must be in [1, DT_MAX_K]");
+    DT_CHECK_ARG(n_probe >= 1 && n_probe <= MAX_PROBE && n_probe <= ix->K, "n_probe out of range");
+    if (nq == 0) return DT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    float *qemb = nullptr;
+    DT_CUDA_TRY(cudaMallocAsync((void **)&qemb, (size_t)nq * D * 4, s));
+    if (int r = enc_embed(enc, d_q, nq, nullptr, qemb, s)) return r;
+    const size_t smem = (size_t)ix->K * 4;
+    if (smem > 48 * 1024)
+        DT_CUDA_TRY(cudaFuncSetAttribute(ivf_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem));
+    ivf_search_kernel<<<(unsigned)nq, ST, smem, s>>>(qemb, d_q, nq, ix->cent, ix->K, ix->offsets,
+                                                     ix->db, ix->ids, n_probe, k, d_idx, d_score,
+                                                     nullptr, d_scanned);
+    DT_CUDA_TRY(cudaGetLastError());
+    DT_CUDA_TRY(cudaFreeAsync(qemb, s));
+    return DT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+"""Learned proposal on the GPU (not part of the paper):
+
+- the encoder's forward kernels match the FP64 oracle;
+- the hand-written backward kernels give the oracle's gradient (every
+  layer), and the loss value matches;
+- training steps lower the InfoNCE loss;
+- the inverted-file search ranks candidates exactly: probing every list
+  returns the exact top-k, and with few probes every answer that is found is
+  the exact neighbour's distance or worse (never better than exact).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import idx_np, mixed_db, to_dev
+from oracle import encoder as oe
+from paper_2107_03368_gb300 import dt, learned, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_forward_matches_oracle():
+    enc = learned.Encoder(seed=3)
+    rng = np.random.default_rng(0)
+    p = oe.init_params(5, scale=0.7)
+    enc.set_params(p.astype(np.float32))
+    db = mixed_db(1, 40)
+    e_gpu = enc.embed(to_dev(db)).cpu().numpy()
+    e_orc, _ = oe.forward(oe.unflatten(p.astype(np.float32).astype(np.float64)), db)
+    np.testing.assert_allclose(e_gpu, e_orc, rtol=0, atol=2e-5)
+    e16 = enc.embed(to_dev(db), bf16=True).float().cpu().numpy()
+    np.testing.assert_allclose(e16, e_orc, rtol=0, atol=1e-2)
+
+
+@pytest.mark.parametrize("B", [2, 5])
+def test_gradients_match_oracle(B):
+    enc = learned.Encoder(seed=4)
+    p = oe.init_params(6, scale=0.7).astype(np.float32)
+    enc.set_params(p)
+    db, _ = synth.database(11, 400, per_object=100, pool=10)
+    q, src = synth.queries(11, db, B)
+    tau = 0.2
+    loss = enc.train_step(to_dev(q), to_dev(db[src]), tau=tau, update=False)
+    g = enc.get_grads().astype(np.float64)
+    o_loss, o_g = oe.loss_and_grad(p.astype(np.float64), q, db[src], tau)
+    assert loss == pytest.approx(o_loss, rel=1e-4)
+    o = 0
+    for name, shape in oe.SHAPES:
+        n = int(np.prod(shape))
+        a, b = g[o:o + n], o_g[o:o + n]
+        err = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        assert err < 2e-3, (name, err)
+        o += n
+    assert np.array_equal(enc.get_params(), p)          # update = 0 leaves weights alone
+
+
+def test_training_lowers_the_loss():
+    enc = learned.Encoder(seed=7)
+    db, _ = synth.database(21, 20_000, per_object=500, pool=20)
+    d_db = to_dev(db)
+
+    def make_queries(r):
+        return synth.queries(1000 + r, db, 2048)[0]
+
+    hist = learned.train(enc, d_db, make_queries, steps=60, batch=128, lr=2e-3, tau=0.1)
+    first = np.mean([l for _, l in hist[:1]])
+    last = np.mean([l for _, l in hist[-2:]])
+    assert last < 0.7 * first, hist
+
+
+def test_ivf_all_lists_is_exact_and_few_lists_never_beat_exact():
+    enc = learned.Encoder(seed=8)
+    db = mixed_db(2, 6000, per_object=300)
+    d_db = to_dev(db)
+    ivf = learned.IVF(enc, d_db, n_lists=64, iters=3)
+    off = ivf.offsets()
+    assert off[0] == 0 and off[-1] == db.shape[0] and np.all(np.diff(off) >= 0)
+    q, _ = synth.queries(3, db, 150)
+    d_q = to_dev(q)
+    idx, score, scanned = ivf.search(d_q, 5, n_probe=64, with_scanned=True)
+    o_idx, o_score, _ = oracle.bf_topk(db, q, 5)
+    assert np.array_equal(idx_np(idx), o_idx)
+    np.testing.assert_allclose(score.cpu().numpy(), o_score, rtol=1e-6, atol=0)
+    assert np.all(scanned.cpu().numpy() == db.shape[0])
+    idx4, score4, sc4 = ivf.search(d_q, 1, n_probe=4, with_scanned=True)
+    s4 = score4.cpu().numpy()[:, 0]
+    assert np.all(s4 >= o_score[:, 0] * (1 - 1e-6))
+    hit = idx_np(idx4)[:, 0] == o_idx[:, 0]
+    assert np.all(np.abs(s4[hit] - o_score[hit, 0]) <= 1e-6 * o_score[hit, 0] + 1e-12)
+    assert np.all(sc4.cpu().numpy() < db.shape[0])
