@@ -17,9 +17,11 @@
 // s_ij = <e_q[i], e_t[j]> / tau, is differentiated by hand back through
 // every layer; Adam updates the parameters.  Kernels are plain FP32 on CUDA
 // cores, one thread per output element (weight gradients split over the
-// batch with atomics).  Inference (enc_embed) is one fused kernel: a CTA
-// takes 4 images, keeps each image's conv activations in shared memory and
-// runs the two dense layers on the 4 pooled feature vectors together.
+// batch with atomics).  Inference (enc_embed) is one fused kernel over
+// weights re-laid out output-channel-contiguous: each thread keeps all
+// output channels of its position in registers (conv2: 64, conv3: 16), a
+// CTA keeps an image's conv activations in shared memory and runs the two
+// dense layers on 4 pooled feature vectors at once.
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -363,12 +365,44 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
 }
 
 // ---------------------------------------------------------------- fused inference
-constexpr int EG = 4;           // images per CTA
+// Weights re-laid out for inference: conv weights [ci][tap][co] and dense
+// weights [in][out], so that a thread's loop over output channels reads
+// contiguous, warp-uniform (conv) or coalesced (dense) addresses.
+constexpr int64_t TW1 = 0, TW2 = TW1 + 9 * C1, TW3 = TW2 + (int64_t)C1 * 9 * C2,
+                  TWF1 = TW3 + (int64_t)C2 * 9 * C3, TWF2 = TWF1 + (int64_t)F0 * F1,
+                  TTOT = TWF2 + (int64_t)F1 * F2;
+
+__global__ void relayout_kernel(const float *__restrict__ P, float *__restrict__ T)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= TTOT) return;
+    float v;
+    if (i < TW2) {                                   // [tap][co] <- [co][0][tap]
+        const int64_t tap = i / C1, co = i % C1;
+        v = P[OW1 + co * 9 + tap];
+    } else if (i < TW3) {                            // [ci][tap][co] <- [co][ci][tap]
+        const int64_t r = i - TW2, co = r % C2, tap = (r / C2) % 9, ci = r / (C2 * 9);
+        v = P[OW2 + (co * C1 + ci) * 9 + tap];
+    } else if (i < TWF1) {
+        const int64_t r = i - TW3, co = r % C3, tap = (r / C3) % 9, ci = r / (C3 * 9);
+        v = P[OW3 + (co * C2 + ci) * 9 + tap];
+    } else if (i < TWF2) {                           // [k][o] <- [o][k]
+        const int64_t r = i - TWF1, o = r % F1, k = r / F1;
+        v = P[OWF1 + o * F0 + k];
+    } else {
+        const int64_t r = i - TWF2, o = r % F2, k = r / F2;
+        v = P[OWF2 + o * F1 + k];
+    }
+    T[i] = v;
+}
+
+constexpr int EG = 4;           // images per CTA pass (dense layers share weight reads)
 constexpr int ET = 256;         // threads
 
-__global__ void __launch_bounds__(ET)
+__global__ void __launch_bounds__(ET, 1)
 embed_kernel(const uint64_t *__restrict__ bits, int64_t n, const float *__restrict__ P,
-             __nv_bfloat16 *__restrict__ out_bf16, float *__restrict__ out_f32)
+             const float *__restrict__ T, __nv_bfloat16 *__restrict__ out_bf16,
+             float *__restrict__ out_f32)
 {
     extern __shared__ float sm[];
     float *a1 = sm;                       // [C1][H1][H1]
@@ -379,122 +413,140 @@ embed_kernel(const uint64_t *__restrict__ bits, int64_t n, const float *__restri
     float *zz = hid + EG * F1;            // [EG][F2]
     __shared__ uint64_t img[kWords];
     const int tid = threadIdx.x;
-    const int64_t g0 = (int64_t)blockIdx.x * EG;
-    for (int gi = 0; gi < EG; ++gi) {
-        const int64_t m = g0 + gi;
-        if (m >= n) break;
-        if (tid < kWords) img[tid] = bits[m * kWords + tid];
-        __syncthreads();
-        for (int i = tid; i < A1; i += ET) {
-            const int x = i % H1, y = (i / H1) % H1, co = i / (H1 * H1);
-            float s = P[OB1 + co];
+    for (int64_t g0 = (int64_t)blockIdx.x * EG; g0 < n; g0 += (int64_t)gridDim.x * EG) {
+        const int gcount = (int)(n - g0 < EG ? n - g0 : EG);
+        for (int gi = 0; gi < gcount; ++gi) {
+            const int64_t m = g0 + gi;
+            if (tid < kWords) img[tid] = bits[m * kWords + tid];
+            __syncthreads();
+            // conv1: four positions per thread, all 32 channels in registers
+            for (int p = tid; p < H1 * H1; p += ET) {
+                const int y = p / H1, x = p % H1;
+                float acc[C1];
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
+                for (int co = 0; co < C1; ++co) acc[co] = P[OB1 + co];
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx)
-                    s += P[OW1 + co * 9 + ky * 3 + kx] * bit_px(img, 2 * y + ky - 1, 2 * x + kx - 1);
-            a1[i] = fmaxf(s, 0.f);
-        }
-        __syncthreads();
-        for (int i = tid; i < A2; i += ET) {
-            const int x = i % H2, y = (i / H2) % H2, co = i / (H2 * H2);
-            float s = P[OB2 + co];
-            for (int ci = 0; ci < C1; ++ci) {
-                const float *wc = P + OW2 + (co * C1 + ci) * 9;
-                const float *sc = a1 + ci * H1 * H1;
+                for (int tap = 0; tap < 9; ++tap) {
+                    if (bit_px(img, 2 * y + tap / 3 - 1, 2 * x + tap % 3 - 1) != 0.f) {
+                        const float4 *w = reinterpret_cast<const float4 *>(T + TW1 + tap * C1);
 #pragma unroll
-                for (int ky = 0; ky < 3; ++ky) {
-                    const int iy = 2 * y + ky - 1;
-                    if (iy < 0) continue;
-#pragma unroll
-                    for (int kx = 0; kx < 3; ++kx) {
-                        const int ix = 2 * x + kx - 1;
-                        if (ix < 0) continue;
-                        s += __ldg(wc + ky * 3 + kx) * sc[iy * H1 + ix];
+                        for (int c4 = 0; c4 < C1 / 4; ++c4) {
+                            const float4 wv = __ldg(w + c4);
+                            acc[4 * c4] += wv.x; acc[4 * c4 + 1] += wv.y;
+                            acc[4 * c4 + 2] += wv.z; acc[4 * c4 + 3] += wv.w;
+                        }
                     }
                 }
+#pragma unroll
+                for (int co = 0; co < C1; ++co) a1[co * H1 * H1 + p] = fmaxf(acc[co], 0.f);
             }
-            a2[i] = fmaxf(s, 0.f);
-        }
-        __syncthreads();
-        for (int i = tid; i < A3; i += ET) {
-            const int x = i % H3, y = (i / H3) % H3, co = i / (H3 * H3);
-            float s = P[OB3 + co];
-            for (int ci = 0; ci < C2; ++ci) {
-                const float *wc = P + OW3 + (co * C2 + ci) * 9;
-                const float *sc = a2 + ci * H2 * H2;
+            __syncthreads();
+            // conv2: one position per thread, all 64 channels in registers
+            {
+                const int p = tid, y = p / H2, x = p % H2;
+                float acc[C2];
 #pragma unroll
-                for (int ky = 0; ky < 3; ++ky) {
-                    const int iy = 2 * y + ky - 1;
-                    if (iy < 0) continue;
+                for (int co = 0; co < C2; ++co) acc[co] = P[OB2 + co];
+                for (int ci = 0; ci < C1; ++ci) {
 #pragma unroll
-                    for (int kx = 0; kx < 3; ++kx) {
-                        const int ix = 2 * x + kx - 1;
-                        if (ix < 0) continue;
-                        s += __ldg(wc + ky * 3 + kx) * sc[iy * H2 + ix];
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int iy = 2 * y + tap / 3 - 1, ix = 2 * x + tap % 3 - 1;
+                        const float v = (iy >= 0 && ix >= 0) ? a1[(ci * H1 + iy) * H1 + ix] : 0.f;
+                        const float4 *w = reinterpret_cast<const float4 *>(T + TW2 + (ci * 9 + tap) * C2);
+#pragma unroll
+                        for (int c4 = 0; c4 < C2 / 4; ++c4) {
+                            const float4 wv = __ldg(w + c4);
+                            acc[4 * c4] += v * wv.x; acc[4 * c4 + 1] += v * wv.y;
+                            acc[4 * c4 + 2] += v * wv.z; acc[4 * c4 + 3] += v * wv.w;
+                        }
                     }
                 }
+#pragma unroll
+                for (int co = 0; co < C2; ++co) a2[co * H2 * H2 + p] = fmaxf(acc[co], 0.f);
             }
-            a3[i] = fmaxf(s, 0.f);
+            __syncthreads();
+            // conv3: 64 positions x 4 blocks of 16 channels
+            {
+                const int p = tid & 63, cb = tid >> 6, y = p / H3, x = p % H3;
+                float acc[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[c] = P[OB3 + cb * 16 + c];
+                for (int ci = 0; ci < C2; ++ci) {
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int iy = 2 * y + tap / 3 - 1, ix = 2 * x + tap % 3 - 1;
+                        const float v = (iy >= 0 && ix >= 0) ? a2[(ci * H2 + iy) * H2 + ix] : 0.f;
+                        const float4 *w =
+                            reinterpret_cast<const float4 *>(T + TW3 + (ci * 9 + tap) * C3 + cb * 16);
+#pragma unroll
+                        for (int c4 = 0; c4 < 4; ++c4) {
+                            const float4 wv = __ldg(w + c4);
+                            acc[4 * c4] += v * wv.x; acc[4 * c4 + 1] += v * wv.y;
+                            acc[4 * c4 + 2] += v * wv.z; acc[4 * c4 + 3] += v * wv.w;
+                        }
+                    }
+                }
+                // a3 overwrites a1, whose last reads (conv2) ended at the barrier above
+#pragma unroll
+                for (int c = 0; c < 16; ++c) a3[(cb * 16 + c) * H3 * H3 + p] = fmaxf(acc[c], 0.f);
+            }
+            __syncthreads();
+            for (int i = tid; i < F0; i += ET) {
+                const int x = i % HP, y = (i / HP) % HP, c = i / (HP * HP);
+                const float *s = a3 + c * H3 * H3;
+                feat[gi * F0 + i] = 0.25f * (s[(2 * y) * H3 + 2 * x] + s[(2 * y) * H3 + 2 * x + 1] +
+                                             s[(2 * y + 1) * H3 + 2 * x] + s[(2 * y + 1) * H3 + 2 * x + 1]);
+            }
+            __syncthreads();
+        }
+        // fc1: thread = output unit, EG images at once, coalesced weight rows
+        for (int o = tid; o < F1; o += ET) {
+            float acc[EG];
+#pragma unroll
+            for (int gi = 0; gi < EG; ++gi) acc[gi] = P[OBF1 + o];
+            for (int k = 0; k < F0; ++k) {
+                const float wk = __ldg(T + TWF1 + (int64_t)k * F1 + o);
+#pragma unroll
+                for (int gi = 0; gi < EG; ++gi) acc[gi] += wk * feat[gi * F0 + k];
+            }
+#pragma unroll
+            for (int gi = 0; gi < EG; ++gi) hid[gi * F1 + o] = fmaxf(acc[gi], 0.f);
         }
         __syncthreads();
-        for (int i = tid; i < F0; i += ET) {
-            const int x = i % HP, y = (i / HP) % HP, c = i / (HP * HP);
-            const float *s = a3 + c * H3 * H3;
-            feat[gi * F0 + i] = 0.25f * (s[(2 * y) * H3 + 2 * x] + s[(2 * y) * H3 + 2 * x + 1] +
-                                         s[(2 * y + 1) * H3 + 2 * x] + s[(2 * y + 1) * H3 + 2 * x + 1]);
+        for (int o = tid; o < F2; o += ET) {
+            float acc[EG];
+#pragma unroll
+            for (int gi = 0; gi < EG; ++gi) acc[gi] = P[OBF2 + o];
+            for (int k = 0; k < F1; ++k) {
+                const float wk = __ldg(T + TWF2 + (int64_t)k * F2 + o);
+#pragma unroll
+                for (int gi = 0; gi < EG; ++gi) acc[gi] += wk * hid[gi * F1 + k];
+            }
+#pragma unroll
+            for (int gi = 0; gi < EG; ++gi) zz[gi * F2 + o] = acc[gi];
         }
         __syncthreads();
-    }
-    const int gcount = (int)(n - g0 < EG ? n - g0 : EG);
-    // fc1: thread = output unit, 16 images at once (weights read once per CTA)
-    for (int o = tid; o < F1; o += ET) {
-        float s[EG];
+        // normalise: warp per image
+        const int lane = tid & 31, wid = tid >> 5;
+        for (int gi = wid; gi < gcount; gi += ET / 32) {
+            float v[4], ss = 0.f;
 #pragma unroll
-        for (int gi = 0; gi < EG; ++gi) s[gi] = P[OBF1 + o];
-        const float *w = P + OWF1 + (int64_t)o * F0;
-        for (int k = 0; k < F0; ++k) {
-            const float wk = __ldg(w + k);
+            for (int j = 0; j < 4; ++j) {
+                v[j] = zz[gi * F2 + lane + 32 * j];
+                ss += v[j] * v[j];
+            }
 #pragma unroll
-            for (int gi = 0; gi < EG; ++gi) s[gi] += wk * feat[gi * F0 + k];
+            for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const float inv = 1.f / fmaxf(sqrtf(ss), 1e-12f);
+            const int64_t m = g0 + gi;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float e = v[j] * inv;
+                if (out_bf16) out_bf16[m * F2 + lane + 32 * j] = __float2bfloat16_rn(e);
+                if (out_f32) out_f32[m * F2 + lane + 32 * j] = e;
+            }
         }
-#pragma unroll
-        for (int gi = 0; gi < EG; ++gi) hid[gi * F1 + o] = fmaxf(s[gi], 0.f);
-    }
-    __syncthreads();
-    for (int o = tid; o < F2; o += ET) {
-        float s[EG];
-#pragma unroll
-        for (int gi = 0; gi < EG; ++gi) s[gi] = P[OBF2 + o];
-        const float *w = P + OWF2 + (int64_t)o * F1;
-        for (int k = 0; k < F1; ++k) {
-            const float wk = __ldg(w + k);
-#pragma unroll
-            for (int gi = 0; gi < EG; ++gi) s[gi] += wk * hid[gi * F1 + k];
-        }
-#pragma unroll
-        for (int gi = 0; gi < EG; ++gi) zz[gi * F2 + o] = s[gi];
-    }
-    __syncthreads();
-    // normalise: warp per image
-    const int lane = tid & 31, wid = tid >> 5;
-    for (int gi = wid; gi < gcount; gi += ET / 32) {
-        float v[4], ss = 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            v[j] = zz[gi * F2 + lane + 32 * j];
-            ss += v[j] * v[j];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        const float inv = 1.f / fmaxf(sqrtf(ss), 1e-12f);
-        const int64_t m = g0 + gi;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float e = v[j] * inv;
-            if (out_bf16) out_bf16[m * F2 + lane + 32 * j] = __float2bfloat16_rn(e);
-            if (out_f32) out_f32[m * F2 + lane + 32 * j] = e;
-        }
+        __syncthreads();
     }
 }
 
@@ -674,9 +726,15 @@ int enc_embed(const dt_encoder *e, const uint64_t *d_bits, int64_t n, uint16_t *
                                     (int)EMBED_SMEM);
     });
     DT_CUDA_TRY(attr);
-    embed_kernel<<<(unsigned)((n + EG - 1) / EG), ET, EMBED_SMEM, s>>>(
-        d_bits, n, e->P, reinterpret_cast<__nv_bfloat16 *>(d_out_bf16), d_out_f32);
+    float *T = nullptr;
+    DT_CUDA_TRY(cudaMallocAsync((void **)&T, (size_t)TTOT * 4, s));
+    relayout_kernel<<<blocks_for(TTOT), 256, 0, s>>>(e->P, T);
+    const int64_t groups = (n + EG - 1) / EG;
+    const unsigned grid = (unsigned)std::min<int64_t>(groups, (int64_t)sm_count());   // one CTA per SM fits
+    embed_kernel<<<grid, ET, EMBED_SMEM, s>>>(d_bits, n, e->P, T,
+                                              reinterpret_cast<__nv_bfloat16 *>(d_out_bf16), d_out_f32);
     DT_CUDA_TRY(cudaGetLastError());
+    DT_CUDA_TRY(cudaFreeAsync(T, s));
     return DT_OK;
 }
 
