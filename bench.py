@@ -6,8 +6,10 @@ Workload (synthetic, seeded): 10,000,000 QUICCI-like descriptors (64x64 bits,
 object) and 10,000 queries made from database descriptors with 30% of their
 set bits cleared and 0.5% of all bits flipped.  One step = one Dissimilarity
 Tree search (dt_search) of the whole 10,000-query batch for the top-10 by
-Eq. 1, against a tree built once beforehand; the GPU brute force (bf_search)
-over the same batch is timed beside it for the tree-vs-brute-force ratio.
+Eq. 1, against a tree built once beforehand.  Beside it: the GPU brute force
+(bf_search, popcount and tensor-core kernels) over the same batch, and the
+learned proposal (encoder trained on the GPU, inverted file, exact rerank)
+at the fewest probed lists that reach recall@1 >= 0.99.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
 host cores instead (a bounded sample of queries per step).
@@ -45,6 +47,11 @@ def parse_args(argv=None):
     p.add_argument("--cpu-sample", type=int, default=32, help="queries the oracle times")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--bf-steps", type=int, default=1, help="timed brute-force passes")
+    p.add_argument("--no-learned", action="store_true", help="skip the learned proposal leg")
+    p.add_argument("--train-steps", type=int, default=1500, help="encoder training steps")
+    p.add_argument("--train-batch", type=int, default=256)
+    p.add_argument("--n-lists", type=int, default=4096, help="inverted-file lists")
+    p.add_argument("--target-recall", type=float, default=0.99)
     return p.parse_args(argv)
 
 
@@ -291,21 +298,14 @@ def run_ours(a, dist):
     e2e_ms = dist.max(e_s.elapsed_time(e_e) / a.steps)
     e2e_value = aggregate(e2e_ms, a.nq, dist.world)
 
-    # GPU brute force on the same batch (the method's sequential search)
-    bf_out = (torch.empty((a.nq, k), dtype=torch.int32, device=dev),
-              torch.empty((a.nq, k), dtype=torch.float32, device=dev), None)
-    dt.bf_search(d_db, d_q, k, out=bf_out)          # warm
-    torch.cuda.synchronize()
-    b_s = torch.cuda.Event(enable_timing=True)
-    b_e = torch.cuda.Event(enable_timing=True)
-    b_s.record(stream)
-    for _ in range(a.bf_steps):
-        dt.bf_search(d_db, d_q, k, out=bf_out)
-    b_e.record(stream)
-    torch.cuda.synchronize()
-    bf_ms = b_s.elapsed_time(b_e) / a.bf_steps
-    bf_qps = a.nq / (bf_ms / 1000.0)
-    same = bool(torch.equal(bf_out[0], tree_idx))
+    # GPU brute force on the same batch (the method's sequential search), both
+    # kernels: popcount (path 1) and the tcgen05 overlap contraction (path 2)
+    bf = {}
+    for name, path in (("popc", 1), ("tensor", 2)):
+        ms_bf, same = time_bf(dt, d_db, d_q, k, path, a.bf_steps, stream, tree_idx)
+        bf[name] = {"queries_per_s": a.nq / (ms_bf / 1000.0), "ms": ms_bf,
+                    "same_indices_as_tree": same}
+    bf_best = max(v["queries_per_s"] for v in bf.values())
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": dist.world,
@@ -321,11 +321,14 @@ def run_ours(a, dist):
         "e2e": {"value": e2e_value, "unit": "queries/s",
                 "h2d_bytes_per_step": int(a.nq * 512),
                 "d2h_bytes_per_step": int(a.nq * k * 8)},
-        "bf_search": {"queries_per_s": bf_qps, "ms": bf_ms, "same_indices_as_tree": same},
-        "tree_vs_bf_speedup": value / dist.world / bf_qps,
+        "bf_search": bf,
+        "tree_vs_bf_speedup": value / dist.world / bf_best,
         "build_s": build_s,
         "gpu_traversal_per_query": {kk: v / a.nq for kk, v in gst.items()},
     }
+
+    if not a.no_learned:
+        line["learned"] = learned_leg(a, dist, d_db, d_q, db, value / dist.world, bf_best, stream)
 
     # roofline of the dominant kernel (dt_search): algorithmic bytes per query =
     # 512 B x (bounds evaluated + descriptors scanned) of the oracle's best-first
@@ -352,6 +355,89 @@ def run_ours(a, dist):
         print(json.dumps(line), flush=True)
     ix.free()
     return 0
+
+
+def time_bf(dt, d_db, d_q, k, path, steps, stream, ref_idx):
+    """Mean CUDA-event time of one bf_search pass over the batch, and whether
+    its indices equal ref_idx."""
+    import torch
+    out = (torch.empty_like(ref_idx), torch.empty(ref_idx.shape, dtype=torch.float32,
+                                                  device=ref_idx.device), None)
+    dt.bf_search(d_db, d_q, k, out=out, path=path)          # warm
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for _ in range(steps):
+        dt.bf_search(d_db, d_q, k, out=out, path=path)
+    e.record(stream)
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / steps, bool(torch.equal(out[0], ref_idx))
+
+
+def learned_leg(a, dist, d_db, d_q, db, tree_qps, bf_qps, stream):
+    """Learned proposal on the same database and queries: train the encoder on
+    (query, exact nearest neighbour) pairs from the GPU brute force, build the
+    inverted file, then find the fewest probed lists whose exact-reranked
+    top-1 reaches the target recall against the exact top-1, and time the
+    search there."""
+    import torch
+    from paper_2107_03368_gb300 import dt, learned, synth
+
+    exact = dt.bf_search(d_db, d_q, 1, path=2)[0][:, 0].clone()
+    enc = learned.Encoder(seed=1)
+
+    def make_queries(r):            # training queries: disjoint seeds from the timed batch
+        return synth.queries(SEED + 5_000_000 + 1000 * dist.rank + r, db, 16384)[0]
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = learned.train(enc, d_db, make_queries, steps=a.train_steps, batch=a.train_batch,
+                         lr=1e-3, tau=0.05)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ivf = learned.IVF(enc, d_db, n_lists=a.n_lists, iters=4)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+
+    def run(probe, reps):
+        ivf.search(d_q, 1, probe)
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(reps):
+            idx, _, scanned = ivf.search(d_q, 1, probe, with_scanned=True)
+        e.record(stream)
+        torch.cuda.synchronize()
+        rec = float((idx[:, 0] == exact).float().mean().item())
+        return s.elapsed_time(e) / reps, rec, float(scanned.float().mean().item())
+
+    sweep = []
+    chosen = None
+    probe = 1
+    while probe <= a.n_lists:
+        ms, rec, scanned = run(probe, 1)
+        sweep.append({"n_probe": probe, "recall_at_1": rec, "ms": ms,
+                      "scanned_per_query": scanned})
+        if rec >= a.target_recall:
+            chosen = probe
+            break
+        probe *= 2
+    out = {"train_steps": a.train_steps, "train_pairs": a.train_steps * a.train_batch,
+           "train_s": train_s, "loss_first": hist[0][1], "loss_last": hist[-1][1],
+           "ivf_build_s": build_s, "n_lists": a.n_lists, "sweep": sweep,
+           "target_recall_at_1": a.target_recall}
+    if chosen is not None:
+        ms, rec, scanned = run(chosen, 3)
+        qps = a.nq / (ms / 1000.0)
+        out.update(n_probe=chosen, recall_at_1=rec, queries_per_s=qps, ms=ms,
+                   scanned_per_query=scanned, speedup_vs_tree=qps / tree_qps,
+                   speedup_vs_bf=qps / bf_qps)
+    ivf.free()
+    enc.free()
+    return out
 
 
 def main(argv=None):
