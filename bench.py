@@ -48,10 +48,16 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--bf-steps", type=int, default=1, help="timed brute-force passes")
     p.add_argument("--no-learned", action="store_true", help="skip the learned proposal leg")
+    p.add_argument("--no-votes", action="store_true", help="skip the partial-retrieval leg")
+    p.add_argument("--votes-queries", type=int, default=1000)
+    p.add_argument("--votes-sample", type=int, default=20,
+                   help="partial queries counted in full (threshold 0)")
     p.add_argument("--train-steps", type=int, default=1500, help="encoder training steps")
     p.add_argument("--train-batch", type=int, default=256)
     p.add_argument("--n-lists", type=int, default=4096, help="inverted-file lists")
     p.add_argument("--target-recall", type=float, default=0.99)
+    p.add_argument("--untrained-baseline", type=int, default=1,
+                   help="also sweep the encoder at its initial weights (1/0)")
     return p.parse_args(argv)
 
 
@@ -155,13 +161,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def measured_peaks():
+def peaks():
+    """Roofline denominators: the measured copy bandwidth and cuBLAS bf16
+    rate of this GPU type, else the stated fallback figures."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "kind": "measured"}
     except Exception:
-        return 6800.0, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0,
+                "kind": "fallback"}
+
+
+def measured_peaks():
+    p = peaks()
+    return p["hbm_gbs"], p["kind"]
 
 
 # ---------------------------------------------------------------------------
@@ -306,6 +321,21 @@ def run_ours(a, dist):
         bf[name] = {"queries_per_s": a.nq / (ms_bf / 1000.0), "ms": ms_bf,
                     "same_indices_as_tree": same}
     bf_best = max(v["queries_per_s"] for v in bf.values())
+    # their own rooflines: the popcount kernel is bound by the POPC pipe
+    # (16 POPC per SM per clock), the tensor kernel by the FP8 tensor rate
+    pk = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    popc_peak = sms * 16 * pk["sm_max_mhz"] * 1e6 / 1e12            # tera-POPC/s
+    popc_ach = a.nq * a.n * 128 / (bf["popc"]["ms"] / 1e3) / 1e12
+    bf["popc"]["roofline"] = {"bound": "alu", "achieved": popc_ach, "peak": popc_peak,
+                              "unit": "TPOPC32/s", "frac": popc_ach / popc_peak,
+                              "peak_kind": "%d SMs x 16 POPC/clk x %.0f MHz" % (sms, pk["sm_max_mhz"])}
+    tc_ach = 2.0 * a.nq * a.n * 4096 / (bf["tensor"]["ms"] / 1e3) / 1e12
+    tc_peak = 2.0 * pk["bf16_tflops"]
+    bf["tensor"]["roofline"] = {"bound": "tensor", "achieved": tc_ach, "peak": tc_peak,
+                                "unit": "TFLOP/s", "frac": tc_ach / tc_peak,
+                                "peak_kind": "FP8 = 2 x %s bf16 %.1f TFLOP/s (nominal ratio)"
+                                             % (pk["kind"], pk["bf16_tflops"])}
 
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": dist.world,
@@ -327,8 +357,11 @@ def run_ours(a, dist):
         "gpu_traversal_per_query": {kk: v / a.nq for kk, v in gst.items()},
     }
 
+    if not a.no_votes:
+        line["votes"] = votes_leg(a, dev, stream, nt)
     if not a.no_learned:
-        line["learned"] = learned_leg(a, dist, d_db, d_q, db, value / dist.world, bf_best, stream)
+        line["learned"] = learned_leg(a, dist, d_db, d_q, db, value / dist.world, bf_best, stream,
+                                      ix, tree_idx)
 
     # roofline of the dominant kernel (dt_search): algorithmic bytes per query =
     # 512 B x (bounds evaluated + descriptors scanned) of the oracle's best-first
@@ -375,7 +408,26 @@ def time_bf(dt, d_db, d_q, k, path, steps, stream, ref_idx):
     return s.elapsed_time(e) / steps, bool(torch.equal(out[0], ref_idx))
 
 
-def learned_leg(a, dist, d_db, d_q, db, tree_qps, bf_qps, stream):
+def warm_start_leg(a, ix, d_q, seeds, tree_idx, stream, probe):
+    """dt_search_seeded over the batch (exact; same indices as the plain
+    tree search), timed like the main step, with its traversal counts."""
+    import torch
+    from paper_2107_03368_gb300 import dt
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    idx, _, _, _ = dt.dt_search_seeded(ix, d_q, a.k, seeds)
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e)
+    _, _, _, st = dt.dt_search_seeded(ix, d_q, a.k, seeds, stats=True)
+    return {"n_probe": probe, "queries_per_s": a.nq / (ms / 1000.0), "ms": ms,
+            "same_indices_as_tree": bool(torch.equal(idx, tree_idx)),
+            "per_query": {kk: v / a.nq for kk, v in st.items()}}
+
+
+def learned_leg(a, dist, d_db, d_q, db, tree_qps, bf_qps, stream, ix, tree_idx):
     """Learned proposal on the same database and queries: train the encoder on
     (query, exact nearest neighbour) pairs from the GPU brute force, build the
     inverted file, then find the fewest probed lists whose exact-reranked
@@ -429,14 +481,96 @@ def learned_leg(a, dist, d_db, d_q, db, tree_qps, bf_qps, stream):
            "train_s": train_s, "loss_first": hist[0][1], "loss_last": hist[-1][1],
            "ivf_build_s": build_s, "n_lists": a.n_lists, "sweep": sweep,
            "target_recall_at_1": a.target_recall}
+    # the same network at its initial weights (what training adds)
+    if a.untrained_baseline:
+        enc0 = learned.Encoder(seed=1)
+        ivf0 = learned.IVF(enc0, d_db, n_lists=a.n_lists, iters=4)
+        un = []
+        for row in sweep:
+            idx0, _, _ = ivf0.search(d_q, 1, row["n_probe"])
+            un.append({"n_probe": row["n_probe"],
+                       "recall_at_1": float((idx0[:, 0] == exact).float().mean().item())})
+        out["untrained_sweep"] = un
+        ivf0.free()
+        enc0.free()
+    # warm start: the proposal's top-k (few probes) seeds the exact tree search
+    ws_probe = 8
+    seeds, _, _ = ivf.search(d_q, a.k, ws_probe)
+    out["warm_start"] = warm_start_leg(a, ix, d_q, seeds, tree_idx, stream, ws_probe)
     if chosen is not None:
+        # the per-query CUDA-core scan at the same setting, for comparison
+        ivf.search(d_q, 1, chosen, path=1)
+        torch.cuda.synchronize()
+        s1 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        s1.record(stream)
+        ivf.search(d_q, 1, chosen, path=1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["per_query_cuda_core_path_ms"] = s1.elapsed_time(e1)
         ms, rec, scanned = run(chosen, 3)
         qps = a.nq / (ms / 1000.0)
+        # the exact rerank is an overlap contraction over the probed rows
+        tf = 2.0 * 4096 * scanned * a.nq / (ms / 1e3) / 1e12
+        tc_peak = 2.0 * peaks()["bf16_tflops"]
         out.update(n_probe=chosen, recall_at_1=rec, queries_per_s=qps, ms=ms,
                    scanned_per_query=scanned, speedup_vs_tree=qps / tree_qps,
-                   speedup_vs_bf=qps / bf_qps)
+                   speedup_vs_bf=qps / bf_qps,
+                   scan_roofline={"bound": "tensor", "achieved": tf, "peak": tc_peak,
+                                  "unit": "TFLOP/s", "frac": tf / tc_peak,
+                                  "note": "2 x 4096 FLOP per (query, scanned row); time of the "
+                                          "whole search call (embedding, probing, scan, merge)"})
     ivf.free()
     enc.free()
+    return out
+
+
+def votes_leg(a, dev, stream, nt):
+    """Batched partial-object retrieval: 400 objects x 25,000 descriptors,
+    1,000 uneven partial queries (contiguous 5-40% of one object, clamped to
+    500-10,000 descriptors), all in one retrieve_objects call.  Threshold 10
+    (the paper's vote threshold) over all queries, and threshold 0 (count
+    every descriptor) over a sample of queries."""
+    import torch
+    from paper_2107_03368_gb300 import dt, synth
+    seed = SEED + 1                      # the partial-retrieval workload's own seed
+    n_obj, per = 400, 25_000
+    db, obj = synth.database(seed, n_obj * per, per_object=per, nthreads=nt)
+    qd, off, qobj = synth.partial_queries(seed, db, n_obj, per, a.votes_queries, nthreads=nt)
+    d_db = torch.from_numpy(db.view(np.int64)).to(dev)
+    ix = dt.dt_build(d_db)
+    d_obj = torch.from_numpy(obj.view(np.int32)).to(dev)
+    d_qd = torch.from_numpy(qd.view(np.int64)).to(dev)
+    d_off = torch.from_numpy(off).to(dev)
+    out = {"workload": "%d objects x %d descriptors, %d partial queries, %d query descriptors"
+                       % (n_obj, per, a.votes_queries, qd.shape[0])}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        r = fn()
+        e.record(stream)
+        torch.cuda.synchronize()
+        return s.elapsed_time(e), r
+
+    ms, (votes, winner, consumed) = timed(lambda: dt.retrieve_objects(
+        ix, d_obj, n_obj, d_qd, d_off, 10, seed, engine=2))
+    w = winner.cpu().numpy()
+    out["threshold_10"] = {
+        "engine": "tensor rounds", "ms": ms, "partial_queries_per_s": a.votes_queries / (ms / 1e3),
+        "descriptors_consumed": int(consumed.sum().item()),
+        "winner_is_source_object": float(np.mean(w == qobj))}
+    m = a.votes_sample
+    sub_off = d_off[: m + 1].contiguous()
+    n_desc = int(off[m])
+    ms0, _ = timed(lambda: dt.retrieve_objects(ix, d_obj, n_obj, d_qd[:n_desc], sub_off, 0, seed,
+                                               engine=2))
+    out["threshold_0_sample"] = {
+        "engine": "tensor", "partial_queries": m, "query_descriptors": n_desc, "ms": ms0,
+        "descriptor_nn_per_s": n_desc / (ms0 / 1e3)}
+    ix.free()
     return out
 
 

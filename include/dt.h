@@ -150,6 +150,24 @@ int dt_search(const dt_index *index, const uint64_t *d_q, int64_t nq, int32_t k,
               void *stream);
 
 /*
+ * dt_search_seeded — dt_search with a warm start.  The paper's query (§4.2)
+ * starts with an empty result list; here the caller may name, per query,
+ * up to n_seed candidate database indices (for instance the answers of the
+ * learned proposal).  Their exact keys are computed first, and the k-th
+ * smallest of them, which can only be >= the exact k-th result's key, caps
+ * the pruning threshold from the first node on.  The result is exactly
+ * dt_search's (same indices, scores and (A, B)); only the work changes.
+ *
+ * d_seed: [nq][n_seed] uint32 original database indices; 0xFFFFFFFF (or any
+ * index >= n) means "no candidate"; duplicates count once.  n_seed in
+ * [0, 4096]; n_seed = 0 is plain dt_search.  Fewer than k valid distinct
+ * candidates give no cap.  Other arguments, outputs and errors as dt_search.
+ */
+int dt_search_seeded(const dt_index *index, const uint64_t *d_q, int64_t nq, int32_t k,
+                     const uint32_t *d_seed, int32_t n_seed, uint32_t *d_idx, float *d_score,
+                     uint16_t *d_ab, dt_stats *h_stats, void *stream);
+
+/*
  * bf_search — exact k nearest database descriptors by scanning all of them
  * (the sequential search of §6.2).
  *
@@ -301,9 +319,14 @@ int ivf_offsets(const dt_ivf *ivf, int64_t *h_offsets);      /* host [n_lists + 
 /* Top-k of each query among the rows of its n_probe nearest lists (by
  * embedding), ranked exactly by Eq. 1 (A*Z + B*P, ties by original index).
  * d_idx/d_score [nq][k] as in dt_search; d_scanned [nq] rows examined (nullable).
- * With n_probe = n_lists the result is the exact top-k. */
+ * With n_probe = n_lists the result is the exact top-k.  n_probe <= 256.
+ * path: 1 = one thread block per query scanning its lists on CUDA cores;
+ * 2 = the (query, list) pairs regrouped by list, each list's rows scanned
+ * once for all its queries on the tensor cores (as bf_search path 2);
+ * 0 = 2 for nq >= 128, else 1.  Both give the same results. */
 int ivf_search(const dt_ivf *ivf, const dt_encoder *enc, const uint64_t *d_q, int64_t nq, int32_t k,
-               int32_t n_probe, uint32_t *d_idx, float *d_score, int64_t *d_scanned, void *stream);
+               int32_t n_probe, uint32_t *d_idx, float *d_score, int64_t *d_scanned, int32_t path,
+               void *stream);
 
 /* Release an index (NULL is allowed).  Synchronises the device it lives on. */
 void dt_free(dt_index *index);

@@ -157,6 +157,28 @@ int dt_search(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k, ui
     return launch_dt_search(ix, d_q, nq, k, d_idx, d_score, d_ab, h_stats, (cudaStream_t)stream);
 }
 
+int dt_search_seeded(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k,
+                     const uint32_t *d_seed, int32_t n_seed, uint32_t *d_idx, float *d_score,
+                     uint16_t *d_ab, dt_stats *h_stats, void *stream)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
+    if (int r = check_k(k)) return r;
+    DT_CHECK_ARG(nq >= 0 && nq < (1LL << 31), "nq out of range");
+    DT_CHECK_ARG(n_seed >= 0 && n_seed <= 4096, "n_seed must be in [0, 4096]");
+    if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
+    if (nq == 0) return DT_OK;
+    REQUIRE_DEV(d_q, "d_q");
+    REQUIRE_DEV(d_idx, "d_idx");
+    REQUIRE_DEV(d_score, "d_score");
+    if (d_ab) REQUIRE_DEV(d_ab, "d_ab");
+    if (n_seed == 0)
+        return launch_dt_search(ix, d_q, nq, k, d_idx, d_score, d_ab, h_stats, (cudaStream_t)stream);
+    REQUIRE_DEV(d_seed, "d_seed");
+    return launch_dt_search_seeded(ix, d_q, nq, k, d_seed, n_seed, d_idx, d_score, d_ab, h_stats,
+                                   (cudaStream_t)stream);
+}
+
 int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,
               uint32_t *d_idx, float *d_score, uint16_t *d_ab, int32_t path, void *stream)
 {

@@ -117,7 +117,7 @@ int dt_autotune(const dt_index *ix, const uint64_t *d_db, int64_t n, const uint6
                 if (threads * bps > 2048) continue;
                 TuneCfg c{threads, bps};
                 float ms = time_call([&] {
-                    return launch_dt_search_cfg(ix, d_q, nq, k, idx, score, nullptr, nullptr, s, &c);
+                    return launch_dt_search_cfg(ix, d_q, nq, k, idx, score, nullptr, nullptr, s, &c, nullptr, 0);
                 }, s);
                 ++tried;
                 if (ms > 0.f && ms < best_ms) {

@@ -24,6 +24,11 @@
 //     per TMEM sub-partition splitting the columns): read the finished
 //     accumulator in 32-column slices while the next tile is being
 //     multiplied into the other accumulator, rank candidates, keep top-k.
+//     A slice is first tested as a whole: from its largest overlap and the
+//     smallest |t| of its 32 rows (a warp minimum taken by the producers)
+//     follows a lower bound on every key in it, and when that bound exceeds
+//     the query's k-th key the slice is skipped — almost every slice, once
+//     the list holds near neighbours.
 // A four-stage mbarrier ring connects producers and MMA; all waits are
 // bounded and a shared abort flag makes every role leave together.  Work
 // units are (128-query tile, database split); per-split lists are merged
@@ -63,7 +68,7 @@ struct TcCtl {
 };
 
 constexpr size_t STAGE_BYTES = (size_t)STAGES * (A_STAGE + B_STAGE);
-constexpr size_t SMEM_BYTES = STAGE_BYTES + sizeof(TcCtl) + 2 * TN * 4 + 1024;
+constexpr size_t SMEM_BYTES = STAGE_BYTES + sizeof(TcCtl) + 2 * TN * 4 + 2 * (TN / 32) * 4 + 1024;
 
 __device__ uint32_t g_tc_error;  // a bounded wait gave up (DT_ETIMEOUT)
 
@@ -132,6 +137,35 @@ __global__ void widen_queries_kernel(const uint64_t *__restrict__ q, int64_t nq,
     }
 }
 
+// Gathered query tiles: row r of tile mt is query slot_q[mt * TM + r]
+// (negative: a zero row); tiles at or beyond *n_tiles are left alone.
+__global__ void widen_gather_kernel(const uint64_t *__restrict__ q, const int32_t *__restrict__ slot_q,
+                                    const int64_t *__restrict__ n_tiles, int64_t max_tiles,
+                                    unsigned char *__restrict__ a_exp, uint32_t *__restrict__ qpop)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (tile, row, chunk)
+    if (id >= max_tiles * TM * NCHUNK) return;
+    const int c = (int)(id % NCHUNK);
+    const int row = (int)((id / NCHUNK) % TM);
+    const int64_t mt = id / ((int64_t)NCHUNK * TM);
+    if (mt >= *n_tiles) return;
+    const int32_t qi = slot_q[mt * TM + row];
+    uint4 bits = make_uint4(0, 0, 0, 0);
+    if (qi >= 0) bits = __ldg(reinterpret_cast<const uint4 *>(q + (int64_t)qi * kWords) + c);
+    store_row_chunk(a_exp + ((size_t)mt * NCHUNK + c) * A_STAGE, row, bits);
+    if (c == 0) {
+        uint32_t s = 0;
+        if (qi >= 0) {
+            const uint4 *r = reinterpret_cast<const uint4 *>(q + (int64_t)qi * kWords);
+            for (int j = 0; j < 32; ++j) {
+                uint4 v = __ldg(r + j);
+                s += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+        }
+        qpop[mt * TM + row] = s;
+    }
+}
+
 // Bounded wait that also gives up when another role aborted.  The thread
 // sleeps inside try_wait (up to 0.5 us per poll) instead of spinning, so
 // waiting warps leave the issue slots to the working ones.
@@ -159,8 +193,8 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, TcCtl 
 struct TcArgs {
     const uint64_t *db;              // database rows [n][64]
     int64_t n;
-    const unsigned char *a_exp;      // pre-widened queries
-    const uint32_t *qpop;            // |q|
+    const unsigned char *a_exp;      // pre-widened query tiles
+    const uint32_t *qpop;            // |q| per query-tile row
     const uint32_t *idx_map;         // row -> reported index (nullable: identity)
     int64_t nq;
     int k;
@@ -168,14 +202,67 @@ struct TcArgs {
     int64_t n_ntiles;
     int64_t tiles_per_split;
     int n_split;
-    uint64_t *partial;               // [2 n_split][nq][k]: two column halves per split
+    // Unit table (list mode): when non-null, unit u is units[u] and the
+    // unit count is read from *n_units; otherwise units are (query tile,
+    // database split) pairs of the whole database.
+    const TcUnit *units;
+    const int64_t *n_units;
+    uint64_t *partial;               // split mode: [2 n_split][nq][k]; list mode: [slot][2][k]
     uint32_t *err;
 };
 
-// 16 bytes (chunk c) of database row t, zeros past n.
-__device__ __forceinline__ uint4 load_bits(const TcArgs &a, int64_t t, int c)
+// One work unit: query tile mt against database rows [r0, r1), taken in
+// tiles of TN rows from r0; query rows >= nvalid are padding.
+struct Unit {
+    int64_t mt, r0, r1, ntiles, sp;
+    int nvalid;
+};
+
+__device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
 {
-    if (t >= a.n) return make_uint4(0, 0, 0, 0);
+    Unit v;
+    if (a.units) {
+        const TcUnit t = a.units[u];
+        v.mt = t.a_tile;
+        v.r0 = t.row0;
+        v.r1 = t.row1;
+        v.ntiles = (t.row1 - t.row0 + TN - 1) / TN;
+        v.sp = 0;
+        v.nvalid = t.nvalid;
+    } else {
+        v.mt = u % a.n_mtiles;
+        v.sp = u / a.n_mtiles;
+        const int64_t t0 = v.sp * a.tiles_per_split;
+        const int64_t t1 = min(a.n_ntiles, t0 + a.tiles_per_split);
+        v.r0 = t0 * TN;
+        v.r1 = a.n;
+        v.ntiles = t1 - t0;
+        v.nvalid = (int)min((int64_t)TM, a.nq - v.mt * TM);
+    }
+    return v;
+}
+
+__device__ __forceinline__ int64_t unit_count(const TcArgs &a)
+{
+    return a.units ? *a.n_units : (int64_t)a.n_mtiles * a.n_split;
+}
+
+// The first unit at or after u (in steps of the grid) that has rows.
+__device__ __forceinline__ int64_t next_busy(const TcArgs &a, int64_t u, int64_t total, Unit &uv)
+{
+    for (; u < total; u += gridDim.x) {
+        uv = get_unit(a, u);
+        if (uv.ntiles > 0) break;
+    }
+    return u;
+}
+
+// 16 bytes (chunk c) of row `row` of tile lt of unit uv, zeros past its end.
+__device__ __forceinline__ uint4 load_bits(const TcArgs &a, const Unit &uv, int64_t lt, int row,
+                                           int c)
+{
+    const int64_t t = uv.r0 + lt * TN + row;
+    if (t >= uv.r1) return make_uint4(0, 0, 0, 0);
     return __ldg(reinterpret_cast<const uint4 *>(a.db + t * kWords) + c);
 }
 
@@ -206,6 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
     unsigned char *stageB = smem + (size_t)STAGES * A_STAGE;        // [STAGES][B_STAGE]
     TcCtl *ctl = reinterpret_cast<TcCtl *>(smem + STAGE_BYTES);
     uint32_t *tpop_s = reinterpret_cast<uint32_t *>(smem + STAGE_BYTES + sizeof(TcCtl));  // [2][TN]
+    uint32_t *tmin_s = tpop_s + 2 * TN;          // [2][TN / 32]: smallest |t| of each 32 rows
     uint32_t *err = args.err;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -231,8 +319,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
-    const int64_t n_mtiles = args.n_mtiles;
-    const int64_t total_units = n_mtiles * args.n_split;
+    const int64_t total_units = unit_count(args);
 
     if (warp >= EPI_WARPS && warp < MMA_WARP) {
         // ------------------------------------------------ producers
@@ -243,38 +330,30 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
         const int row = pw * 32 + lane;
         constexpr int G = 4;                       // chunks per load group
         uint32_t g = 0, tile = 0, tp_acc = 0;
-        int64_t u = blockIdx.x, nt = 0, t1 = 0;
+        Unit uv{};
+        int64_t u = next_busy(args, blockIdx.x, total_units, uv), lt = 0;
         int grp = 0;
-        if (u < total_units) {
-            const int64_t sp = u / n_mtiles;
-            nt = sp * args.tiles_per_split;
-            t1 = min(args.n_ntiles, nt + args.tiles_per_split);
-        }
         uint4 nx[G];
 #pragma unroll
         for (int i = 0; i < G; ++i)
-            nx[i] = u < total_units ? load_bits(args, nt * TN + row, i) : make_uint4(0, 0, 0, 0);
+            nx[i] = u < total_units ? load_bits(args, uv, 0, row, i) : make_uint4(0, 0, 0, 0);
         while (u < total_units) {
-            const int64_t mt = u % n_mtiles;
+            const int64_t mt = uv.mt;
             const int cur_grp = grp;
             uint4 cu[G];
 #pragma unroll
             for (int i = 0; i < G; ++i) cu[i] = nx[i];
-            // advance (u, nt, grp) and prefetch the next group
+            // advance (u, lt, grp) and prefetch the next group
             if (++grp == NCHUNK / G) {
                 grp = 0;
-                if (++nt == t1) {
-                    u += gridDim.x;
-                    if (u < total_units) {
-                        const int64_t sp = u / n_mtiles;
-                        nt = sp * args.tiles_per_split;
-                        t1 = min(args.n_ntiles, nt + args.tiles_per_split);
-                    }
+                if (++lt == uv.ntiles) {
+                    lt = 0;
+                    u = next_busy(args, u + gridDim.x, total_units, uv);
                 }
             }
             if (u < total_units) {
 #pragma unroll
-                for (int i = 0; i < G; ++i) nx[i] = load_bits(args, nt * TN + row, grp * G + i);
+                for (int i = 0; i < G; ++i) nx[i] = load_bits(args, uv, lt, row, grp * G + i);
             }
 #pragma unroll
             for (int i = 0; i < G; ++i) {
@@ -292,6 +371,8 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 tp_acc += __popc(cu[i].x) + __popc(cu[i].y) + __popc(cu[i].z) + __popc(cu[i].w);
                 if (c == NCHUNK - 1) {                 // row complete: |t| for the epilogue
                     tpop_s[(tile & 1u) * TN + row] = tp_acc;
+                    const uint32_t mn = __reduce_min_sync(0xffffffffu, tp_acc);
+                    if (lane == 0) tmin_s[(tile & 1u) * (TN / 32) + pw] = mn;
                     tp_acc = 0;
                     ++tile;
                 }
@@ -306,10 +387,8 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
         if (lane == 0) {
             uint32_t g = 0, t = 0;
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
-                const int64_t sp = u / n_mtiles;
-                const int64_t t0 = sp * args.tiles_per_split;
-                const int64_t t1 = min(args.n_ntiles, t0 + args.tiles_per_split);
-                for (int64_t nt = t0; nt < t1; ++nt, ++t) {
+                const Unit uv = get_unit(args, u);
+                for (int64_t lt = 0; lt < uv.ntiles; ++lt, ++t) {
                     const uint32_t acc = t & 1u, ra = t >> 1;
                     if (!wait_or_abort(&ctl->acc_empty[acc], (ra & 1u) ^ 1u, ctl, err)) goto mma_done;
                     tc_fence_after();
@@ -346,31 +425,45 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
         const int row = quarter * 32 + lane;         // TMEM lane = query row of the tile
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         const int k = args.k;
-        const int64_t n = args.n, nq = args.nq;
+        const int64_t nq = args.nq;
         uint64_t L[kMaxK];
         uint32_t t = 0;
         for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x) {
-            const int64_t mt = u % n_mtiles, sp = u / n_mtiles;
-            const int64_t t0 = sp * args.tiles_per_split;
-            const int64_t t1 = min(args.n_ntiles, t0 + args.tiles_per_split);
-            const int64_t qi = mt * TM + row;
-            const QueryWeights w = query_weights(qi < nq ? args.qpop[qi] : 0u);
+            const Unit uv = get_unit(args, u);
+            const int64_t qi = uv.mt * TM + row;       // query (split mode) or pair slot (list mode)
+            const bool valid = row < uv.nvalid;
+            const QueryWeights w = query_weights(valid ? args.qpop[qi] : 0u);
             // key = A*Z + B*P = (|q| - O) Z + (|t| - O) P = |t| P + |q| Z - O (Z + P)
             const uint32_t qz = w.pop * w.Z, zp = w.Z + w.P;
             for (int j = 0; j < k; ++j) L[j] = kEmpty;
             uint64_t worst = kEmpty;
             uint32_t wkey = 0xFFFFFFFFu;      // key part of `worst`
-            for (int64_t nt = t0; nt < t1; ++nt, ++t) {
+            for (int64_t lt = 0; lt < uv.ntiles; ++lt, ++t) {
                 const uint32_t acc = t & 1u, ra = t >> 1;
                 if (!warp_wait(&ctl->acc_full[acc], ra & 1u, ctl, err, lane)) goto done;
                 tc_fence_after();
-                const int64_t base = nt * TN;
+                const int64_t base = uv.r0 + lt * TN;
                 for (int cb = half * (TN / 64); cb < (half + 1) * (TN / 64); ++cb) {
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(lane_base + acc * (uint32_t)TN + cb * 32, v);
                     tmem_ld_wait();
+                    // Slice filter: every key here is >= |t|min P + |q| Z - Omax (Z + P);
+                    // when that exceeds the k-th key no row of the slice can enter
+                    // the list.  The values are non-negative floats, ordered as
+                    // their bit patterns.
+                    if (wkey != 0xFFFFFFFFu) {
+                        uint32_t mx = 0;
+#pragma unroll
+                        for (int j = 0; j < 32; j += 2) mx = __vimax3_u32(mx, v[j], v[j + 1]);
+                        const uint32_t omax =
+                            __float_as_uint(fmaf(__uint_as_float(mx), 4096.0f, 8388608.0f)) -
+                            0x4B000000u;
+                        const uint32_t tmin = tmin_s[(t & 1u) * (TN / 32) + cb];
+                        if ((int64_t)omax * zp < (int64_t)qz + (int64_t)tmin * w.P - (int64_t)wkey)
+                            continue;
+                    }
                     const int64_t b0 = base + cb * 32;
-                    const int m = (int)(n - b0 < 32 ? n - b0 : 32);
+                    const int m = (int)(uv.r1 - b0 < 32 ? uv.r1 - b0 : 32);
                     const uint32_t *tp = tpop_s + (t & 1u) * TN + cb * 32;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
@@ -389,9 +482,11 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
             }
-            if (qi < nq)
-                for (int j = 0; j < k; ++j)
-                    args.partial[((int64_t)(2 * sp + half) * nq + qi) * k + j] = L[j];
+            if (valid) {
+                uint64_t *out = args.units ? args.partial + (qi * 2 + half) * k
+                                           : args.partial + ((2 * uv.sp + half) * nq + qi) * k;
+                for (int j = 0; j < k; ++j) out[j] = L[j];
+            }
         }
     }
 done:
@@ -468,6 +563,8 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.n_ntiles = n_ntiles;
     a.tiles_per_split = tiles_per_split;
     a.n_split = n_split;
+    a.units = nullptr;
+    a.n_units = nullptr;
     a.partial = partial;
     a.err = err;
     bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
@@ -487,6 +584,47 @@ int take_tc_error(bool *raised)
     DT_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(v)));
     if (v) DT_CUDA_TRY(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(zero)));
     *raised = v != 0;
+    return DT_OK;
+}
+
+int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
+                    const int32_t *slot_q, const TcUnit *units, const int64_t *n_units,
+                    int64_t max_units, int k, uint64_t *partial, cudaStream_t s)
+{
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM_BYTES);
+    });
+    DT_CUDA_TRY(attr_err);
+    if (max_units <= 0) return DT_OK;
+    unsigned char *a_exp = nullptr;
+    uint32_t *qpop = nullptr, *err = nullptr;
+    DT_CUDA_TRY(cudaMallocAsync((void **)&a_exp, (size_t)max_units * NCHUNK * A_STAGE, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&qpop, (size_t)max_units * TM * 4, s));
+    DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
+    const int64_t items = max_units * TM * NCHUNK;
+    widen_gather_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, slot_q, n_units,
+                                                                        max_units, a_exp, qpop);
+    DT_CUDA_TRY(cudaGetLastError());
+    TcArgs a{};
+    a.db = db;
+    a.n = n;
+    a.a_exp = a_exp;
+    a.qpop = qpop;
+    a.idx_map = idx_map;
+    a.nq = max_units * TM;
+    a.k = k;
+    a.units = units;
+    a.n_units = n_units;
+    a.partial = partial;
+    a.err = err;
+    const int grid = (int)std::min<int64_t>(max_units, sm_count());
+    bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
+    DT_CUDA_TRY(cudaGetLastError());
+    DT_CUDA_TRY(cudaFreeAsync(qpop, s));
+    DT_CUDA_TRY(cudaFreeAsync(a_exp, s));
     return DT_OK;
 }
 

@@ -104,13 +104,17 @@ __device__ __forceinline__ uint32_t node_bound(const TreeView &tv, int nd, uint4
 
 // Search one query; `slot` is the warp's sorted top-k list (must start
 // kEmpty).  `stack` is this warp's private stack of depth+1 entries.
+// `cap` is a key known to be >= the exact k-th result's key (the k-th
+// smallest key of k database descriptors found beforehand, or ~0u): a
+// subtree is skipped when its bound exceeds min(cap, current k-th key), so
+// a good cap prunes from the first node on and the result stays exact.
 // Returns false if the stack would overflow (cannot happen for a stack of
 // depth+1 entries; checked anyway).
 template <bool USE_AND>
 __device__ __forceinline__ bool warp_tree_search(const TreeView &tv, uint4 qv,
                                                  const QueryWeights &w, int k, uint64_t *stack,
                                                  int stack_cap, int lane, uint64_t &slot,
-                                                 TraverseStats &st)
+                                                 TraverseStats &st, uint32_t cap = ~0u)
 {
     int sp = 0;
     {
@@ -125,7 +129,7 @@ __device__ __forceinline__ bool warp_tree_search(const TreeView &tv, uint4 qv,
         uint64_t e = shfl_u64(lane == 0 ? stack[sp] : 0ull, 0);
         uint32_t lb = (uint32_t)(e >> 32);
         int nd = (int)(uint32_t)e;
-        uint32_t worst = (uint32_t)(shfl_u64(slot, k - 1) >> 32);
+        uint32_t worst = min(cap, (uint32_t)(shfl_u64(slot, k - 1) >> 32));
         if (lb > worst) continue;
         for (;;) {
             const NodeRec rec = tv.node[nd];
@@ -149,7 +153,7 @@ __device__ __forceinline__ bool warp_tree_search(const TreeView &tv, uint4 qv,
                 lbd += (bb >> 16) * w.P;
             }
             st.bounds += 2;
-            worst = (uint32_t)(shfl_u64(slot, k - 1) >> 32);
+            worst = min(cap, (uint32_t)(shfl_u64(slot, k - 1) >> 32));
             const bool sim_first = lbs <= lbd;
             const int near = sim_first ? s : d, far = sim_first ? d : s;
             const uint32_t lbn = sim_first ? lbs : lbd, lbf = sim_first ? lbd : lbs;

@@ -183,7 +183,8 @@ ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ q
                   const float *__restrict__ cent, int K, const int64_t *__restrict__ offsets,
                   const uint64_t *__restrict__ ivf_db, const uint32_t *__restrict__ ivf_ids,
                   int n_probe, int k, uint32_t *__restrict__ idx, float *__restrict__ score,
-                  uint16_t *__restrict__ ab, int64_t *__restrict__ scanned)
+                  uint16_t *__restrict__ ab, int64_t *__restrict__ scanned,
+                  int32_t *__restrict__ probe_out)
 {
     extern __shared__ float csc[];                   // [K] centroid scores
     __shared__ float qe[D];
@@ -194,9 +195,9 @@ ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ q
     const int64_t q = blockIdx.x;
     if (tid < D) qe[tid] = qemb[q * D + tid];
     __syncthreads();
-    for (int c = tid; c < K; c += ST) {
+    for (int c = tid; c < K; c += ST) {       // centroids stored [D][K]: coalesced
         float s = 0.f;
-        for (int d = 0; d < D; ++d) s += qe[d] * __ldg(cent + (int64_t)c * D + d);
+        for (int d = 0; d < D; ++d) s += qe[d] * __ldg(cent + (int64_t)d * K + c);
         csc[c] = s;
     }
     __syncthreads();
@@ -223,6 +224,15 @@ ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ q
             csc[c] = -INFINITY;
         }
         __syncthreads();
+    }
+    if (probe_out) {                          // list-major path: hand the lists over
+        if (tid < n_probe) probe_out[q * n_probe + tid] = probe[tid];
+        if (tid == 0 && scanned) {
+            int64_t rows = 0;
+            for (int p = 0; p < n_probe; ++p) rows += offsets[probe[p] + 1] - offsets[probe[p]];
+            scanned[q] = rows;
+        }
+        return;
     }
     // exact scan of the probed lists: warps take 32-row blocks in turn
     const uint4 qv = __ldg(reinterpret_cast<const uint4 *>(qs + q * kWords) + lane);
@@ -284,6 +294,107 @@ ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ q
     (void)ab;
 }
 
+// ------------------------------------------------ list-major search on the tensor cores
+// The (query, probed list) pairs are regrouped by list; each list's rows
+// are then scanned once for all the queries that probe it, 128 queries per
+// tensor-core tile (launch_tc_units), and every query merges the top-k
+// lists of its pairs.
+__global__ void pair_count_kernel(const int32_t *__restrict__ probe, int64_t pairs,
+                                  int32_t *__restrict__ counts)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < pairs; i += stride) atomicAdd(&counts[probe[i]], 1);
+}
+
+// One block: per list, ceil(count / 128) units, numbered list by list.
+__global__ void unit_plan_kernel(const int32_t *__restrict__ counts, int K,
+                                 const int64_t *__restrict__ offsets, int64_t *__restrict__ unit_base,
+                                 TcUnit *__restrict__ units, int64_t *__restrict__ n_units)
+{
+    __shared__ uint32_t tmp[33];
+    uint32_t run = 0;
+    for (int c0 = 0; c0 < K; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const uint32_t cnt = c < K ? (uint32_t)counts[c] : 0u;
+        const uint32_t nu = (cnt + kTcTileM - 1) / kTcTileM;
+        uint32_t total;
+        const uint32_t before = block_excl_scan(nu, tmp, &total);
+        if (c < K) {
+            const int64_t b = (int64_t)run + before;
+            unit_base[c] = b;
+            for (uint32_t i = 0; i < nu; ++i) {
+                TcUnit u;
+                u.row0 = offsets[c];
+                u.row1 = offsets[c + 1];
+                u.a_tile = (int32_t)(b + i);
+                u.nvalid = (int32_t)min(cnt - i * kTcTileM, (uint32_t)kTcTileM);
+                units[b + i] = u;
+            }
+        }
+        run += total;
+    }
+    if (threadIdx.x == 0) *n_units = run;
+}
+
+// Pair (q, p) -> a row of one of its list's units.
+__global__ void pair_scatter_kernel(const int32_t *__restrict__ probe, int64_t nq, int n_probe,
+                                    const int64_t *__restrict__ unit_base, int32_t *__restrict__ fill,
+                                    int32_t *__restrict__ slot_q, int64_t *__restrict__ slot_of)
+{
+    const int64_t pairs = nq * n_probe;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < pairs; i += stride) {
+        const int c = probe[i];
+        const int r = atomicAdd(&fill[c], 1);
+        const int64_t slot = (unit_base[c] + r / kTcTileM) * kTcTileM + r % kTcTileM;
+        slot_q[slot] = (int32_t)(i / n_probe);
+        slot_of[i] = slot;
+    }
+}
+
+// One warp per query: merge the two column-half lists of each of its
+// pairs; write idx and score.
+__global__ void pair_merge_kernel(const uint64_t *__restrict__ partial,
+                                  const int64_t *__restrict__ slot_of, int n_probe,
+                                  const uint64_t *__restrict__ qs, int64_t nq, int k,
+                                  uint32_t *__restrict__ idx, float *__restrict__ score)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= nq) return;
+    uint64_t slot = kEmpty;
+    for (int p = 0; p < n_probe; ++p) {
+        const int64_t sl = slot_of[q * n_probe + p];
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t c = lane < k ? partial[(sl * 2 + h) * k + lane] : kEmpty;
+            warp_list_merge(slot, c, k, lane);
+        }
+    }
+    const uint4 qv = __ldg(reinterpret_cast<const uint4 *>(qs + q * kWords) + lane);
+    const QueryWeights w = query_weights(warp_sum(popc4(qv)));
+    if (lane < k) {
+        const int64_t o = q * k + lane;
+        if (slot == kEmpty) {
+            idx[o] = 0xFFFFFFFFu;
+            score[o] = __int_as_float(0x7f800000);
+        } else {
+            idx[o] = (uint32_t)slot;
+            score[o] = key_score(w, (uint32_t)(slot >> 32));
+        }
+    }
+}
+
+__global__ void transpose_centroids_kernel(const float *__restrict__ cent, int K,
+                                           float *__restrict__ cent_t)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)K * D) return;
+    const int64_t c = i / D, d = i % D;
+    cent_t[d * K + c] = cent[i];
+}
+
 }  // namespace
 }  // namespace dtk
 
@@ -292,6 +403,7 @@ struct dt_ivf {
     int64_t n = 0;
     int K = 0;
     float *cent = nullptr;          // [K][128]
+    float *cent_t = nullptr;        // [128][K] (search reads it coalesced)
     int64_t *offsets = nullptr;     // [K+1]
     uint64_t *db = nullptr;         // [n][64] cluster order
     uint32_t *ids = nullptr;        // [n] original index
@@ -326,6 +438,7 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
         cudaMallocAsync((void **)&counts, (size_t)K * 4, s) != cudaSuccess ||
         cudaMallocAsync((void **)&sums, (size_t)K * D * 4, s) != cudaSuccess ||
         cudaMalloc((void **)&ix->cent, (size_t)K * D * 4) != cudaSuccess ||
+        cudaMalloc((void **)&ix->cent_t, (size_t)K * D * 4) != cudaSuccess ||
         cudaMalloc((void **)&ix->offsets, (size_t)(K + 1) * 8) != cudaSuccess ||
         cudaMalloc((void **)&ix->db, (size_t)n * 512) != cudaSuccess ||
         cudaMalloc((void **)&ix->ids, (size_t)n * 4) != cudaSuccess) {
@@ -350,6 +463,8 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
         cudaMemsetAsync(counts, 0, (size_t)K * 4, s);
         scatter_kernel<<<(unsigned)std::min<int64_t>((n + 7) / 8, 8192), 256, 0, s>>>(
             d_db, n, assign, ix->offsets, counts, ix->db, ix->ids);
+        transpose_centroids_kernel<<<(unsigned)(((int64_t)K * D + 255) / 256), 256, 0, s>>>(
+            ix->cent, K, ix->cent_t);
         if (cudaGetLastError() != cudaSuccess) fail("kernel launch");
     }
     cudaFreeAsync(sums, s);
@@ -358,7 +473,8 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
     cudaFreeAsync(emb, s);
     if (cudaStreamSynchronize(s) != cudaSuccess && rc == DT_OK) fail("stream");
     if (rc != DT_OK) {
-        cudaFree(ix->cent); cudaFree(ix->offsets); cudaFree(ix->db); cudaFree(ix->ids);
+        cudaFree(ix->cent); cudaFree(ix->cent_t); cudaFree(ix->offsets); cudaFree(ix->db);
+        cudaFree(ix->ids);
         delete ix;
         return rc;
     }
@@ -370,7 +486,8 @@ void ivf_free(dt_ivf *ix)
 {
     if (!ix) return;
     cudaDeviceSynchronize();
-    cudaFree(ix->cent); cudaFree(ix->offsets); cudaFree(ix->db); cudaFree(ix->ids);
+    cudaFree(ix->cent); cudaFree(ix->cent_t); cudaFree(ix->offsets); cudaFree(ix->db);
+    cudaFree(ix->ids);
     delete ix;
 }
 
@@ -383,13 +500,17 @@ int ivf_offsets(const dt_ivf *ix, int64_t *h_offsets)
 }
 
 int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int64_t nq, int32_t k,
-               int32_t n_probe, uint32_t *d_idx, float *d_score, int64_t *d_scanned, void *stream)
+               int32_t n_probe, uint32_t *d_idx, float *d_score, int64_t *d_scanned, int32_t path,
+               void *stream)
 {
     DT_CHECK_ARG(ix && enc && d_q && d_idx && d_score && nq >= 0, "bad arguments");
     DT_CHECK_ARG(k >= 1 && k <= DT_MAX_K, "k must be in [1, DT_MAX_K]");
     DT_CHECK_ARG(n_probe >= 1 && n_probe <= MAX_PROBE && n_probe <= ix->K, "n_probe out of range");
+    DT_CHECK_ARG(path >= 0 && path <= 2, "path must be 0, 1 or 2");
+    DT_CHECK_ARG(nq <= (1LL << 31) / MAX_PROBE, "nq out of range");
     if (nq == 0) return DT_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool tensor = path == 2 || (path == 0 && nq >= kTcTileM);
     float *qemb = nullptr;
     DT_CUDA_TRY(cudaMallocAsync((void **)&qemb, (size_t)nq * D * 4, s));
     if (int r = enc_embed(enc, d_q, nq, nullptr, qemb, s)) return r;
@@ -397,12 +518,57 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     if (smem > 48 * 1024)
         DT_CUDA_TRY(cudaFuncSetAttribute(ivf_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem));
-    ivf_search_kernel<<<(unsigned)nq, ST, smem, s>>>(qemb, d_q, nq, ix->cent, ix->K, ix->offsets,
+    if (!tensor) {
+        ivf_search_kernel<<<(unsigned)nq, ST, smem, s>>>(qemb, d_q, nq, ix->cent_t, ix->K,
+                                                         ix->offsets, ix->db, ix->ids, n_probe, k,
+                                                         d_idx, d_score, nullptr, d_scanned, nullptr);
+        DT_CUDA_TRY(cudaGetLastError());
+        DT_CUDA_TRY(cudaFreeAsync(qemb, s));
+        return DT_OK;
+    }
+    // list-major: probes -> pairs grouped by list -> tensor-core units -> merge
+    const int64_t pairs = nq * n_probe;
+    const int64_t max_units = std::min<int64_t>(pairs, (pairs + kTcTileM - 1) / kTcTileM + ix->K);
+    int32_t *probe = nullptr, *counts = nullptr, *slot_q = nullptr;
+    int64_t *unit_base = nullptr, *n_units = nullptr, *slot_of = nullptr;
+    TcUnit *units = nullptr;
+    uint64_t *partial = nullptr;
+    DT_CUDA_TRY(cudaMallocAsync((void **)&probe, (size_t)pairs * 4, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&counts, (size_t)ix->K * 4 * 2, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&unit_base, (size_t)ix->K * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&n_units, 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&units, (size_t)max_units * sizeof(TcUnit), s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&slot_q, (size_t)max_units * kTcTileM * 4, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&slot_of, (size_t)pairs * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)max_units * kTcTileM * 2 * k * 8, s));
+    int32_t *fill = counts + ix->K;
+    DT_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ix->K * 4 * 2, s));
+    DT_CUDA_TRY(cudaMemsetAsync(slot_q, 0xFF, (size_t)max_units * kTcTileM * 4, s));
+    ivf_search_kernel<<<(unsigned)nq, ST, smem, s>>>(qemb, d_q, nq, ix->cent_t, ix->K, ix->offsets,
                                                      ix->db, ix->ids, n_probe, k, d_idx, d_score,
-                                                     nullptr, d_scanned);
+                                                     nullptr, d_scanned, probe);
+    const unsigned pb = (unsigned)std::min<int64_t>((pairs + 255) / 256, 8192);
+    pair_count_kernel<<<pb, 256, 0, s>>>(probe, pairs, counts);
+    unit_plan_kernel<<<1, 1024, 0, s>>>(counts, ix->K, ix->offsets, unit_base, units, n_units);
+    pair_scatter_kernel<<<pb, 256, 0, s>>>(probe, nq, n_probe, unit_base, fill, slot_q, slot_of);
     DT_CUDA_TRY(cudaGetLastError());
+    int rc = launch_tc_units(ix->db, ix->n, ix->ids, d_q, slot_q, units, n_units, max_units, k,
+                             partial, s);
+    if (rc == DT_OK) {
+        pair_merge_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(partial, slot_of, n_probe, d_q,
+                                                                   nq, k, d_idx, d_score);
+        DT_CUDA_TRY(cudaGetLastError());
+    }
+    cudaFreeAsync(partial, s);
+    cudaFreeAsync(slot_of, s);
+    cudaFreeAsync(slot_q, s);
+    cudaFreeAsync(units, s);
+    cudaFreeAsync(n_units, s);
+    cudaFreeAsync(unit_base, s);
+    cudaFreeAsync(counts, s);
+    cudaFreeAsync(probe, s);
     DT_CUDA_TRY(cudaFreeAsync(qemb, s));
-    return DT_OK;
+    return rc;
 }
 
 }  // extern "C"

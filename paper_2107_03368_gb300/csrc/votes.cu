@@ -17,7 +17,7 @@
 //  * tensor: batches of descriptors are scanned against the index's
 //    tree-ordered database on the tensor cores (bf_tc.cu, rows reported as
 //    original indices).  With T = 0 all descriptors form one batch.  With
-//    T > 0 the draws are taken in rounds — the next 32, 64, 128 ... drawn
+//    T > 0 the draws are taken in rounds — the next T, 2T, 4T ... drawn
 //    descriptors of every undecided query — and a replay kernel advances
 //    each query's vote count in draw order, so only the descriptors the
 //    loop of §3 actually consumes (plus the rest of their round) are searched.
@@ -357,7 +357,9 @@ int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects
     draw_order_kernel<<<(nq + 127) / 128, 128, 0, s>>>(qoffsets, nq, seed, order);
     DT_CUDA_TRY(cudaGetLastError());
     int rc = DT_OK;
-    int64_t C = std::max<int64_t>(32, 2 * (int64_t)threshold);
+    // A query needs at least T draws to reach T votes, so the first round
+    // takes exactly T; later rounds double.
+    int64_t C = std::max<int64_t>(1, (int64_t)threshold);
     for (;;) {
         round_plan_kernel<<<1, 1024, 0, s>>>(qoffsets, nq, C, st);
         int64_t batch_n = 0;

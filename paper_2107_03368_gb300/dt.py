@@ -77,6 +77,7 @@ def load():
             "dt_get_info": ([P, P], ctypes.c_int),
             "dt_export": ([P, P, P, P, P, P, P, P], ctypes.c_int),
             "dt_search": ([P, P, i64, i32, P, P, P, P, P], ctypes.c_int),
+            "dt_search_seeded": ([P, P, i64, i32, P, i32, P, P, P, P, P], ctypes.c_int),
             "bf_search": ([P, i64, P, i64, i32, P, P, P, i32, P], ctypes.c_int),
             "bf_search_noalloc": ([P, i64, P, i64, i32, P, P, P, P], ctypes.c_int),
             "retrieve_objects": ([P, P, i32, P, P, i32, i64, i32, u64, P, P, P, i32, P],
@@ -192,6 +193,26 @@ def dt_search(index: Index, q, k, with_ab=False, stats=False, out=None, stream=N
     _check(load().dt_search(index.handle, _ptr(q), q.shape[0], k, _ptr(idx), _ptr(score),
                             _ptr(ab), ctypes.byref(st) if st is not None else None,
                             _stream(stream)), "dt_search")
+    return idx, score, ab, (st.as_dict() if st is not None else None)
+
+
+def dt_search_seeded(index: Index, q, k, seeds, with_ab=False, stats=False, out=None,
+                     stream=None):
+    """dt_search with a warm start from candidate indices seeds [nq, n_seed]
+    (int32/uint32 device tensor, -1 = none).  Same results as dt_search."""
+    q = _desc(q, "q")
+    if seeds.dim() != 2 or seeds.shape[0] != q.shape[0]:
+        raise ValueError("seeds must be [nq, n_seed]")
+    if seeds.dtype not in (torch.int32, torch.uint32) or not seeds.is_contiguous():
+        raise ValueError("seeds must be a contiguous int32 tensor")
+    if seeds.device != q.device:
+        raise ValueError("seeds must be on the queries' device")
+    idx, score, ab = _outputs(q.shape[0], k, q.device, with_ab, out)
+    st = Stats() if stats else None
+    _check(load().dt_search_seeded(index.handle, _ptr(q), q.shape[0], k, _ptr(seeds),
+                                   seeds.shape[1], _ptr(idx), _ptr(score), _ptr(ab),
+                                   ctypes.byref(st) if st is not None else None,
+                                   _stream(stream)), "dt_search_seeded")
     return idx, score, ab, (st.as_dict() if st is not None else None)
 
 

@@ -36,7 +36,7 @@ def _lib():
             "ivf_build": ([P, P, i64, i32, i32, P, P], ctypes.c_int),
             "ivf_free": ([P], None),
             "ivf_offsets": ([P, P], ctypes.c_int),
-            "ivf_search": ([P, P, P, i64, i32, i32, P, P, P, P], ctypes.c_int),
+            "ivf_search": ([P, P, P, i64, i32, i32, P, P, P, i32, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -125,14 +125,17 @@ class IVF:
         dt._check(_lib().ivf_offsets(self._h, ctypes.c_void_p(out.ctypes.data)), "ivf_offsets")
         return out
 
-    def search(self, q, k, n_probe, with_scanned=False, stream=None):
+    def search(self, q, k, n_probe, with_scanned=False, path=0, stream=None):
+        """path: 0 auto, 1 CUDA cores (a block per query), 2 tensor cores
+        (list-major); identical results."""
         q = dt._desc(q, "q")
         nq = q.shape[0]
         idx = torch.empty((nq, k), dtype=torch.int32, device=q.device)
         score = torch.empty((nq, k), dtype=torch.float32, device=q.device)
         scanned = torch.empty(nq, dtype=torch.int64, device=q.device) if with_scanned else None
         dt._check(_lib().ivf_search(self._h, self.enc.handle, _p(q), nq, k, n_probe, _p(idx),
-                                    _p(score), _p(scanned), dt._stream(stream)), "ivf_search")
+                                    _p(score), _p(scanned), path, dt._stream(stream)),
+                  "ivf_search")
         return idx, score, scanned
 
     def free(self):

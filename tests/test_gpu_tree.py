@@ -95,3 +95,48 @@ def test_ties_at_the_bound_on_gpu():
         for k in (1, 2, 5):
             idx, score, ab, _ = dt.dt_search(ix, to_dev(q), k, with_ab=True)
             assert_matches_oracle(db, q, k, idx, score, ab)
+
+
+@pytest.mark.parametrize("k", [1, 10])
+def test_seeded_search_is_exact_for_any_seeds(k):
+    """Warm start: whatever the candidates (exact answers, random, absent,
+    repeated, out of range, fewer than k), the result is the oracle's; good
+    candidates only remove work."""
+    import torch
+    db = mixed_db(41, 20000, per_object=500)
+    q = edge_queries(42, db, 300)
+    d_db, d_q = to_dev(db), to_dev(q)
+    ix = dt.dt_build(d_db)
+    nq = q.shape[0]
+    o_idx, _, _ = oracle.bf_topk(db, q, k)
+    rng = np.random.default_rng(5)
+    exact = np.where(o_idx < 0, -1, o_idx).astype(np.int64)
+    variants = {
+        "exact": exact,
+        "random": rng.integers(0, db.shape[0], size=(nq, 2 * k)),
+        "absent": np.full((nq, 3), -1),
+        "repeated": np.repeat(exact[:, :1], 2 * k, axis=1),
+        "out_of_range": np.concatenate([exact[:, : max(k - 1, 1)],
+                                        np.full((nq, 2), db.shape[0] + 7)], axis=1),
+    }
+    _, _, _, plain = dt.dt_search(ix, d_q, k, stats=True)
+    for name, seeds in variants.items():
+        s = torch.from_numpy(seeds.astype(np.int64).astype(np.uint32).view(np.int32)).cuda()
+        idx, score, ab, st = dt.dt_search_seeded(ix, d_q, k, s.contiguous(), with_ab=True,
+                                                 stats=True)
+        assert_matches_oracle(db, q, k, idx, score, ab)
+        if name == "exact":
+            assert st["descs_scanned"] <= plain["descs_scanned"], (st, plain)
+            assert st["bounds_evaluated"] <= plain["bounds_evaluated"]
+
+
+def test_seeded_search_with_no_seeds_is_plain_search():
+    import torch
+    w = synth.workload_small()
+    ix = dt.dt_build(to_dev(w["db"]))
+    d_q = to_dev(w["q"])
+    a = dt.dt_search(ix, d_q, 5, stats=True)
+    b = dt.dt_search_seeded(ix, d_q, 5, torch.empty((d_q.shape[0], 0), dtype=torch.int32,
+                                                    device=d_q.device), stats=True)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert a[3] == b[3]
