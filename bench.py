@@ -174,6 +174,34 @@ def peaks():
                 "kind": "fallback"}
 
 
+# DRAM traffic of one dt_search launch on this workload (10M descriptors,
+# 10,000 queries, top-10), dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture of this script's timed launch.  It describes the kernel
+# source it was captured from; any change to that source voids it.
+DT_SEARCH_TRAFFIC = {"bytes": 51.47e12 + 0.955e12,
+                     "sources_sha1": "1a51aa971bfa393306848fb88a6d078554b53ade"}
+DT_SEARCH_SOURCES = ("paper_2107_03368_gb300/csrc/dt_search.cu",
+                     "paper_2107_03368_gb300/csrc/dt_traverse.cuh")
+
+
+def dt_search_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for rel in DT_SEARCH_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def dt_search_traffic(a):
+    """Captured traffic per launch, or None when it does not apply."""
+    if (a.n, a.nq, a.k) != (10_000_000, 10_000, 10) or DT_SEARCH_TRAFFIC["bytes"] is None:
+        return None
+    if DT_SEARCH_TRAFFIC["sources_sha1"] != dt_search_sources_sha1():
+        return None
+    return DT_SEARCH_TRAFFIC["bytes"]
+
+
 def measured_peaks():
     p = peaks()
     return p["hbm_gbs"], p["kind"]
@@ -368,7 +396,7 @@ def run_ours(a, dist):
     # search, measured on the cpu_baseline sample
     peak, peak_kind = measured_peaks()
     roof = {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-            "traffic": None, "peak_kind": peak_kind}
+            "traffic": dt_search_traffic(a), "peak_kind": peak_kind}
     if dist.rank == 0 and not a.no_cpu_baseline:
         sample = min(a.cpu_sample, a.nq)
         cpu_qps, ost, _ = oracle_tree_leg(db, q_all, k, sample, nt)

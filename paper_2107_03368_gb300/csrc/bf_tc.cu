@@ -10,18 +10,21 @@
 // exact.  The epilogue turns O into the Eq. 1 key (A = |q| - O, B = |t| - O)
 // and keeps per-query top-k.
 //
-// Kernel organisation (one persistent CTA per SM, 17 warps):
-//   * warps 8-15 (producers, one database row per thread): for each 128-bit
-//     K chunk, widen the chunk of 256 database descriptors into a 32 KB
-//     shared-memory stage (K-major 8x16-byte core matrices); each thread
-//     loads the next four chunks (64 bytes) while it widens the current
-//     ones and sums its row's |t| into shared memory.  The
-//     first lane of warp 8 also brings the matching 16 KB chunk of the 128
-//     pre-widened queries with one bulk copy (TMA engine);
-//   * warp 16 (one thread): 4 MMAs of 128 x 256 x 32 per chunk into one of
-//     two TMEM accumulators (256 columns each), then commits to free the stage;
-//   * warps 0-7 (epilogue, one thread per query row = TMEM lane, two warps
-//     per TMEM sub-partition splitting the columns): read the finished
+// Kernel organisation (one persistent CTA per SM, 17 warps).  A work unit
+// is two 128-query tiles against a run of 128-descriptor tiles, so every
+// widened database chunk feeds the MMAs of 256 queries:
+//   * warps 8-15 (producers, half a database row per thread): for each
+//     128-bit K chunk, widen the chunk of 128 database descriptors into a
+//     16 KB shared-memory stage (K-major 8x16-byte core matrices); each
+//     thread loads its next four half-chunks (32 bytes) while it widens the
+//     current ones and sums its half row's |t| into shared memory.  The
+//     first lane of warp 8 also brings the matching 16 KB chunks of the two
+//     pre-widened query tiles with bulk copies (TMA engine);
+//   * warp 16 (one thread): per chunk and query tile, 4 MMAs of
+//     128 x 128 x 32 into that tile's half of one of two TMEM accumulators
+//     (256 columns each), then commits to free the stage;
+//   * warps 0-7 (epilogue, one thread per query row = TMEM lane; warps 0-3
+//     serve the first query tile, 4-7 the second): read the finished
 //     accumulator in 32-column slices while the next tile is being
 //     multiplied into the other accumulator, rank candidates, keep top-k.
 //     A slice is first tested as a whole: from its largest overlap and the
@@ -31,8 +34,8 @@
 //     the list holds near neighbours.
 // A four-stage mbarrier ring connects producers and MMA; all waits are
 // bounded and a shared abort flag makes every role leave together.  Work
-// units are (128-query tile, database split); per-split lists are merged
-// afterwards.
+// units are (pair of query tiles, database split), or come from a unit
+// table (list mode); per-split lists are merged afterwards.
 #include <algorithm>
 #include <mutex>
 
@@ -43,19 +46,23 @@ namespace dtk {
 namespace {
 
 constexpr int TM = 128;                 // queries per tile (MMA M)
-constexpr int TN = 256;                 // descriptors per tile (MMA N)
+constexpr int QT = 2;                   // query tiles per unit
+constexpr int TN = 128;                 // descriptors per tile (MMA N)
 constexpr int KC = 128;                 // K bytes (= bits) per chunk
 constexpr int NCHUNK = kBits / KC;      // 32
 constexpr int STAGES = 4;
-constexpr int A_STAGE = TM * KC;        // 16 KB
-constexpr int B_STAGE = TN * KC;        // 32 KB
+constexpr int A_STAGE = TM * KC;        // 16 KB per query tile
+constexpr int B_STAGE = TN * KC;        // 16 KB
+constexpr int STAGE = QT * A_STAGE + B_STAGE;   // 48 KB
 constexpr uint32_t LBO = 128;           // next core matrix along K
 constexpr uint32_t SBO = (KC / 16) * 128;  // next 8-row group (1024 B)
-constexpr int EPI_WARPS = 8, PROD_WARPS = TN / 32;
+constexpr int EPI_WARPS = 8, PROD_WARPS = 8;    // producers: two per database row
 constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
 constexpr int THREADS = (MMA_WARP + 1) * 32;
-constexpr uint32_t TMEM_COLS = 512;     // two 256-column FP32 accumulators
+constexpr uint32_t ACC_COLS = QT * TN;  // one accumulator: 128 columns per query tile
+constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;    // double-buffered: 512
 constexpr uint32_t IDESC = idesc_e4m3_f32(TM, TN);
+static_assert(TN == 4 * 32 && PROD_WARPS == 2 * (TN / 32), "two producer warps per 32 rows");
 
 struct TcCtl {
     uint64_t full[STAGES];
@@ -67,8 +74,9 @@ struct TcCtl {
     volatile uint32_t abort;
 };
 
-constexpr size_t STAGE_BYTES = (size_t)STAGES * (A_STAGE + B_STAGE);
-constexpr size_t SMEM_BYTES = STAGE_BYTES + sizeof(TcCtl) + 2 * TN * 4 + 2 * (TN / 32) * 4 + 1024;
+constexpr size_t STAGE_BYTES = (size_t)STAGES * STAGE;
+// + |t| halves [2 tiles][2 halves][TN] and their 32-row minima [2][2][TN / 32]
+constexpr size_t SMEM_BYTES = STAGE_BYTES + sizeof(TcCtl) + 2 * 2 * TN * 4 + 2 * 2 * (TN / 32) * 4 + 1024;
 
 __device__ uint32_t g_tc_error;  // a bounded wait gave up (DT_ETIMEOUT)
 
@@ -110,6 +118,18 @@ __device__ __forceinline__ void store_row_chunk(unsigned char *stage, int row, u
         *reinterpret_cast<uint4 *>(stage + core_off(row, 2 * i)) = lo;
         *reinterpret_cast<uint4 *>(stage + core_off(row, 2 * i + 1)) = hi;
     }
+}
+
+// Write 64 bits (half hw of a 128-bit chunk) of one row: pieces 4 hw .. 4 hw + 3.
+__device__ __forceinline__ void store_half_chunk(unsigned char *stage, int row, int hw, uint2 bits)
+{
+    uint4 lo, hi;
+    widen32(bits.x, lo, hi);
+    *reinterpret_cast<uint4 *>(stage + core_off(row, 4 * hw)) = lo;
+    *reinterpret_cast<uint4 *>(stage + core_off(row, 4 * hw + 1)) = hi;
+    widen32(bits.y, lo, hi);
+    *reinterpret_cast<uint4 *>(stage + core_off(row, 4 * hw + 2)) = lo;
+    *reinterpret_cast<uint4 *>(stage + core_off(row, 4 * hw + 3)) = hi;
 }
 
 // Queries -> pre-widened tiles a_exp[m_tile][chunk][16 KB stage image], plus |q|.
@@ -199,6 +219,7 @@ struct TcArgs {
     int64_t nq;
     int k;
     int n_mtiles;
+    int n_mpairs;                    // units per split: ceil(n_mtiles / 2)
     int64_t n_ntiles;
     int64_t tiles_per_split;
     int n_split;
@@ -207,15 +228,17 @@ struct TcArgs {
     // database split) pairs of the whole database.
     const TcUnit *units;
     const int64_t *n_units;
-    uint64_t *partial;               // split mode: [2 n_split][nq][k]; list mode: [slot][2][k]
+    uint64_t *partial;               // split mode: [n_split][nq][k]; list mode: [slot][k]
     uint32_t *err;
 };
 
-// One work unit: query tile mt against database rows [r0, r1), taken in
-// tiles of TN rows from r0; query rows >= nvalid are padding.
+// One work unit: query tiles mt[0], mt[1] (mt[1] < 0: absent) against
+// database rows [r0, r1), taken in tiles of TN rows from r0; query rows
+// >= nvalid[i] of tile i are padding.
 struct Unit {
-    int64_t mt, r0, r1, ntiles, sp;
-    int nvalid;
+    int64_t mt[QT];
+    int64_t r0, r1, ntiles, sp;
+    int nvalid[QT];
 };
 
 __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
@@ -223,28 +246,35 @@ __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
     Unit v;
     if (a.units) {
         const TcUnit t = a.units[u];
-        v.mt = t.a_tile;
+        v.mt[0] = t.a_tile0;
+        v.mt[1] = t.a_tile1;
         v.r0 = t.row0;
         v.r1 = t.row1;
         v.ntiles = (t.row1 - t.row0 + TN - 1) / TN;
         v.sp = 0;
-        v.nvalid = t.nvalid;
+        v.nvalid[0] = t.nvalid0;
+        v.nvalid[1] = t.a_tile1 >= 0 ? t.nvalid1 : 0;
     } else {
-        v.mt = u % a.n_mtiles;
-        v.sp = u / a.n_mtiles;
+        const int64_t mp = u % a.n_mpairs;
+        v.sp = u / a.n_mpairs;
         const int64_t t0 = v.sp * a.tiles_per_split;
         const int64_t t1 = min(a.n_ntiles, t0 + a.tiles_per_split);
         v.r0 = t0 * TN;
         v.r1 = a.n;
         v.ntiles = t1 - t0;
-        v.nvalid = (int)min((int64_t)TM, a.nq - v.mt * TM);
+#pragma unroll
+        for (int i = 0; i < QT; ++i) {
+            const int64_t mt = QT * mp + i;
+            v.mt[i] = mt < a.n_mtiles ? mt : -1;
+            v.nvalid[i] = mt < a.n_mtiles ? (int)min((int64_t)TM, a.nq - mt * TM) : 0;
+        }
     }
     return v;
 }
 
 __device__ __forceinline__ int64_t unit_count(const TcArgs &a)
 {
-    return a.units ? *a.n_units : (int64_t)a.n_mtiles * a.n_split;
+    return a.units ? *a.n_units : (int64_t)a.n_mpairs * a.n_split;
 }
 
 // The first unit at or after u (in steps of the grid) that has rows.
@@ -257,13 +287,14 @@ __device__ __forceinline__ int64_t next_busy(const TcArgs &a, int64_t u, int64_t
     return u;
 }
 
-// 16 bytes (chunk c) of row `row` of tile lt of unit uv, zeros past its end.
-__device__ __forceinline__ uint4 load_bits(const TcArgs &a, const Unit &uv, int64_t lt, int row,
-                                           int c)
+// 8 bytes (half hw of chunk c) of row `row` of tile lt of unit uv, zeros
+// past its end.
+__device__ __forceinline__ uint2 load_half(const TcArgs &a, const Unit &uv, int64_t lt, int row,
+                                           int hw, int c)
 {
     const int64_t t = uv.r0 + lt * TN + row;
-    if (t >= uv.r1) return make_uint4(0, 0, 0, 0);
-    return __ldg(reinterpret_cast<const uint4 *>(a.db + t * kWords) + c);
+    if (t >= uv.r1) return make_uint2(0, 0);
+    return __ldg(reinterpret_cast<const uint2 *>(a.db + t * kWords) + 2 * c + hw);
 }
 
 // Insert a candidate into a thread's sorted top-k list (rare once the list
@@ -289,11 +320,13 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         ((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *stageA = smem;                                   // [STAGES][A_STAGE]
-    unsigned char *stageB = smem + (size_t)STAGES * A_STAGE;        // [STAGES][B_STAGE]
+    unsigned char *stageA = smem;                                   // [STAGES][QT][A_STAGE]
+    unsigned char *stageB = smem + (size_t)STAGES * QT * A_STAGE;   // [STAGES][B_STAGE]
     TcCtl *ctl = reinterpret_cast<TcCtl *>(smem + STAGE_BYTES);
-    uint32_t *tpop_s = reinterpret_cast<uint32_t *>(smem + STAGE_BYTES + sizeof(TcCtl));  // [2][TN]
-    uint32_t *tmin_s = tpop_s + 2 * TN;          // [2][TN / 32]: smallest |t| of each 32 rows
+    // |t| of each row as two half-row sums [tile & 1][half][TN], and the
+    // smallest half sum of each 32 rows [tile & 1][half][TN / 32]
+    uint32_t *tpop_s = reinterpret_cast<uint32_t *>(smem + STAGE_BYTES + sizeof(TcCtl));
+    uint32_t *tmin_s = tpop_s + 2 * 2 * TN;
     uint32_t *err = args.err;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -323,24 +356,26 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
 
     if (warp >= EPI_WARPS && warp < MMA_WARP) {
         // ------------------------------------------------ producers
-        // One database row per thread.  Bits are loaded 64 bytes (four chunks)
-        // at a time, one group ahead of the chunks being widened; |t| is summed
-        // on the way and left in shared memory for the epilogue.
+        // Half a database row per thread (warps 8-11 the first 8 bytes of each
+        // chunk, warps 12-15 the second).  Bits are loaded 32 bytes (four
+        // half-chunks) at a time, one group ahead of the chunks being widened;
+        // |t| is summed on the way and left in shared memory for the epilogue.
         const int pw = warp - EPI_WARPS;
-        const int row = pw * 32 + lane;
+        const int rg = pw & 3, hw = pw >> 2;
+        const int row = rg * 32 + lane;
         constexpr int G = 4;                       // chunks per load group
         uint32_t g = 0, tile = 0, tp_acc = 0;
         Unit uv{};
         int64_t u = next_busy(args, blockIdx.x, total_units, uv), lt = 0;
         int grp = 0;
-        uint4 nx[G];
+        uint2 nx[G];
 #pragma unroll
         for (int i = 0; i < G; ++i)
-            nx[i] = u < total_units ? load_bits(args, uv, 0, row, i) : make_uint4(0, 0, 0, 0);
+            nx[i] = u < total_units ? load_half(args, uv, 0, row, hw, i) : make_uint2(0, 0);
         while (u < total_units) {
-            const int64_t mt = uv.mt;
+            const int64_t mt0 = uv.mt[0], mt1 = uv.mt[1];
             const int cur_grp = grp;
-            uint4 cu[G];
+            uint2 cu[G];
 #pragma unroll
             for (int i = 0; i < G; ++i) cu[i] = nx[i];
             // advance (u, lt, grp) and prefetch the next group
@@ -353,7 +388,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
             }
             if (u < total_units) {
 #pragma unroll
-                for (int i = 0; i < G; ++i) nx[i] = load_bits(args, uv, lt, row, grp * G + i);
+                for (int i = 0; i < G; ++i) nx[i] = load_half(args, uv, lt, row, hw, grp * G + i);
             }
 #pragma unroll
             for (int i = 0; i < G; ++i) {
@@ -362,17 +397,20 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 const uint32_t r = g / STAGES;
                 if (!warp_wait(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err, lane)) goto done;
                 if (pw == 0 && lane == 0) {
-                    mbar_arrive_expect_tx(&ctl->full[s], (uint32_t)A_STAGE);
-                    bulk_g2s(stageA + (size_t)s * A_STAGE,
-                             args.a_exp + ((size_t)mt * NCHUNK + c) * A_STAGE, (uint32_t)A_STAGE,
-                             &ctl->full[s]);
+                    unsigned char *a_dst = stageA + (size_t)s * QT * A_STAGE;
+                    mbar_arrive_expect_tx(&ctl->full[s], (uint32_t)(mt1 >= 0 ? 2 : 1) * A_STAGE);
+                    bulk_g2s(a_dst, args.a_exp + ((size_t)mt0 * NCHUNK + c) * A_STAGE,
+                             (uint32_t)A_STAGE, &ctl->full[s]);
+                    if (mt1 >= 0)
+                        bulk_g2s(a_dst + A_STAGE, args.a_exp + ((size_t)mt1 * NCHUNK + c) * A_STAGE,
+                                 (uint32_t)A_STAGE, &ctl->full[s]);
                 }
-                store_row_chunk(stageB + (size_t)s * B_STAGE, row, cu[i]);
-                tp_acc += __popc(cu[i].x) + __popc(cu[i].y) + __popc(cu[i].z) + __popc(cu[i].w);
-                if (c == NCHUNK - 1) {                 // row complete: |t| for the epilogue
-                    tpop_s[(tile & 1u) * TN + row] = tp_acc;
+                store_half_chunk(stageB + (size_t)s * B_STAGE, row, hw, cu[i]);
+                tp_acc += __popc(cu[i].x) + __popc(cu[i].y);
+                if (c == NCHUNK - 1) {                 // half row complete: |t| part for the epilogue
+                    tpop_s[((tile & 1u) * 2 + hw) * TN + row] = tp_acc;
                     const uint32_t mn = __reduce_min_sync(0xffffffffu, tp_acc);
-                    if (lane == 0) tmin_s[(tile & 1u) * (TN / 32) + pw] = mn;
+                    if (lane == 0) tmin_s[((tile & 1u) * 2 + hw) * (TN / 32) + rg] = mn;
                     tp_acc = 0;
                     ++tile;
                 }
@@ -392,19 +430,24 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                     const uint32_t acc = t & 1u, ra = t >> 1;
                     if (!wait_or_abort(&ctl->acc_empty[acc], (ra & 1u) ^ 1u, ctl, err)) goto mma_done;
                     tc_fence_after();
-                    const uint32_t d_tmem = tmem + acc * (uint32_t)TN;
+                    const uint32_t d_tmem = tmem + acc * ACC_COLS;
+                    const int n_qt = uv.mt[1] >= 0 ? 2 : 1;
                     for (int c = 0; c < NCHUNK; ++c, ++g) {
                         const int s = (int)(g % STAGES);
                         const uint32_t r = g / STAGES;
                         if (!wait_or_abort(&ctl->full[s], r & 1u, ctl, err)) goto mma_done;
                         tc_fence_after();
-                        const uint32_t a_base = smem_u32(stageA + (size_t)s * A_STAGE);
+                        const uint32_t a_base = smem_u32(stageA + (size_t)s * QT * A_STAGE);
                         const uint32_t b_base = smem_u32(stageB + (size_t)s * B_STAGE);
+                        for (int i = 0; i < n_qt; ++i) {
 #pragma unroll
-                        for (int kk = 0; kk < KC / 32; ++kk) {
-                            const uint64_t ad = smem_desc_kmajor(a_base + kk * 2 * LBO, LBO, SBO);
-                            const uint64_t bd = smem_desc_kmajor(b_base + kk * 2 * LBO, LBO, SBO);
-                            mma_e4m3(d_tmem, ad, bd, IDESC, (c | kk) != 0 ? 1u : 0u);
+                            for (int kk = 0; kk < KC / 32; ++kk) {
+                                const uint64_t ad = smem_desc_kmajor(
+                                    a_base + (uint32_t)i * A_STAGE + kk * 2 * LBO, LBO, SBO);
+                                const uint64_t bd = smem_desc_kmajor(b_base + kk * 2 * LBO, LBO, SBO);
+                                mma_e4m3(d_tmem + (uint32_t)i * TN, ad, bd, IDESC,
+                                         (c | kk) != 0 ? 1u : 0u);
+                            }
                         }
                         mma_commit(&ctl->empty[s]);
                     }
@@ -418,10 +461,9 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
         __syncwarp();
     } else {
         // ------------------------------------------------ epilogue (warps 0-7)
-        // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its sub-partition) and
-        // the column half w / 4 of each tile; each half keeps its own top-k
-        // lists, merged later like two more splits.
-        const int quarter = warp & 3, half = warp >> 2;
+        // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its sub-partition) of
+        // query tile w / 4 (that tile's 128 accumulator columns).
+        const int quarter = warp & 3, qt = warp >> 2;
         const int row = quarter * 32 + lane;         // TMEM lane = query row of the tile
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         const int k = args.k;
@@ -430,8 +472,9 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
         uint32_t t = 0;
         for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x) {
             const Unit uv = get_unit(args, u);
-            const int64_t qi = uv.mt * TM + row;       // query (split mode) or pair slot (list mode)
-            const bool valid = row < uv.nvalid;
+            const bool present = uv.mt[qt] >= 0;
+            const int64_t qi = uv.mt[qt] * TM + row;   // query (split mode) or pair slot (list mode)
+            const bool valid = present && row < uv.nvalid[qt];
             const QueryWeights w = query_weights(valid ? args.qpop[qi] : 0u);
             // key = A*Z + B*P = (|q| - O) Z + (|t| - O) P = |t| P + |q| Z - O (Z + P)
             const uint32_t qz = w.pop * w.Z, zp = w.Z + w.P;
@@ -443,9 +486,11 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 if (!warp_wait(&ctl->acc_full[acc], ra & 1u, ctl, err, lane)) goto done;
                 tc_fence_after();
                 const int64_t base = uv.r0 + lt * TN;
-                for (int cb = half * (TN / 64); cb < (half + 1) * (TN / 64); ++cb) {
+                const uint32_t *tp0 = tpop_s + (t & 1u) * 2 * TN, *tp1 = tp0 + TN;
+                const uint32_t *tm0 = tmin_s + (t & 1u) * 2 * (TN / 32), *tm1 = tm0 + TN / 32;
+                for (int cb = 0; cb < (present ? TN / 32 : 0); ++cb) {
                     uint32_t v[32];
-                    tmem_ld_32x32b_x32(lane_base + acc * (uint32_t)TN + cb * 32, v);
+                    tmem_ld_32x32b_x32(lane_base + acc * ACC_COLS + (uint32_t)qt * TN + cb * 32, v);
                     tmem_ld_wait();
                     // Slice filter: every key here is >= |t|min P + |q| Z - Omax (Z + P);
                     // when that exceeds the k-th key no row of the slice can enter
@@ -458,20 +503,20 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                         const uint32_t omax =
                             __float_as_uint(fmaf(__uint_as_float(mx), 4096.0f, 8388608.0f)) -
                             0x4B000000u;
-                        const uint32_t tmin = tmin_s[(t & 1u) * (TN / 32) + cb];
+                        const uint32_t tmin = tm0[cb] + tm1[cb];   // <= min of the row sums
                         if ((int64_t)omax * zp < (int64_t)qz + (int64_t)tmin * w.P - (int64_t)wkey)
                             continue;
                     }
                     const int64_t b0 = base + cb * 32;
                     const int m = (int)(uv.r1 - b0 < 32 ? uv.r1 - b0 : 32);
-                    const uint32_t *tp = tpop_s + (t & 1u) * TN + cb * 32;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         // sum = O * 2^-12 exactly: 4096 * sum + 2^23, read the mantissa
                         const uint32_t o =
                             __float_as_uint(fmaf(__uint_as_float(v[j]), 4096.0f, 8388608.0f)) -
                             0x4B000000u;
-                        const uint32_t key = tp[j] * w.P + qz - o * zp;
+                        const uint32_t tpj = tp0[cb * 32 + j] + tp1[cb * 32 + j];
+                        const uint32_t key = tpj * w.P + qz - o * zp;
                         if (j < m && key <= wkey) {   // rare once the list has filled
                             worst = list_insert(L, k, key, b0 + j, args.idx_map, worst);
                             wkey = (uint32_t)(worst >> 32);
@@ -483,8 +528,8 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
             }
             if (valid) {
-                uint64_t *out = args.units ? args.partial + (qi * 2 + half) * k
-                                           : args.partial + ((2 * uv.sp + half) * nq + qi) * k;
+                uint64_t *out = args.units ? args.partial + qi * k
+                                           : args.partial + (uv.sp * nq + qi) * k;
                 for (int j = 0; j < k; ++j) out[j] = L[j];
             }
         }
@@ -528,16 +573,17 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     });
     DT_CUDA_TRY(attr_err);
     const int n_mtiles = (int)((nq + TM - 1) / TM);
+    const int n_mpairs = (n_mtiles + QT - 1) / QT;
     const int64_t n_ntiles = (n + TN - 1) / TN;
     const int sms = sm_count();
     TuneCfg c{0, 0};
     if (cfg) c = *cfg;
     else tune_lookup(TUNE_TC, n, nq, k, &c);
     const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_ntiles)
-                               : pick_bf_splits(n_mtiles, n_ntiles, sms);
+                               : pick_bf_splits(n_mpairs, n_ntiles, sms);
     const int64_t tiles_per_split = (n_ntiles + splits - 1) / splits;
     const int n_split = (int)((n_ntiles + tiles_per_split - 1) / tiles_per_split);
-    const int64_t units = (int64_t)n_mtiles * n_split;
+    const int64_t units = (int64_t)n_mpairs * n_split;
     const int grid = (int)std::min<int64_t>(units, sms);
 
     unsigned char *a_exp = nullptr;
@@ -546,7 +592,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     const size_t a_bytes = (size_t)n_mtiles * NCHUNK * A_STAGE;
     DT_CUDA_TRY(cudaMallocAsync((void **)&a_exp, a_bytes, s));
     DT_CUDA_TRY(cudaMallocAsync((void **)&qpop, (size_t)nq * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)2 * n_split * nq * k * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)n_split * nq * k * 8, s));
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
     const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
     widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, nq, n_mtiles, a_exp, qpop);
@@ -560,6 +606,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.nq = nq;
     a.k = k;
     a.n_mtiles = n_mtiles;
+    a.n_mpairs = n_mpairs;
     a.n_ntiles = n_ntiles;
     a.tiles_per_split = tiles_per_split;
     a.n_split = n_split;
@@ -572,7 +619,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     cudaFreeAsync(qpop, s);
     cudaFreeAsync(a_exp, s);
     *partial_out = partial;
-    *n_split_out = 2 * n_split;
+    *n_split_out = n_split;
     return DT_OK;
 }
 
@@ -589,7 +636,8 @@ int take_tc_error(bool *raised)
 
 int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
                     const int32_t *slot_q, const TcUnit *units, const int64_t *n_units,
-                    int64_t max_units, int k, uint64_t *partial, cudaStream_t s)
+                    const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
+                    cudaStream_t s)
 {
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
@@ -598,15 +646,15 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
                                         (int)SMEM_BYTES);
     });
     DT_CUDA_TRY(attr_err);
-    if (max_units <= 0) return DT_OK;
+    if (max_tiles <= 0) return DT_OK;
     unsigned char *a_exp = nullptr;
     uint32_t *qpop = nullptr, *err = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&a_exp, (size_t)max_units * NCHUNK * A_STAGE, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&qpop, (size_t)max_units * TM * 4, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&a_exp, (size_t)max_tiles * NCHUNK * A_STAGE, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&qpop, (size_t)max_tiles * TM * 4, s));
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
-    const int64_t items = max_units * TM * NCHUNK;
-    widen_gather_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, slot_q, n_units,
-                                                                        max_units, a_exp, qpop);
+    const int64_t items = max_tiles * TM * NCHUNK;
+    widen_gather_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, slot_q, n_tiles,
+                                                                        max_tiles, a_exp, qpop);
     DT_CUDA_TRY(cudaGetLastError());
     TcArgs a{};
     a.db = db;
@@ -614,13 +662,13 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.a_exp = a_exp;
     a.qpop = qpop;
     a.idx_map = idx_map;
-    a.nq = max_units * TM;
+    a.nq = max_tiles * TM;
     a.k = k;
     a.units = units;
     a.n_units = n_units;
     a.partial = partial;
     a.err = err;
-    const int grid = (int)std::min<int64_t>(max_units, sm_count());
+    const int grid = (int)std::min<int64_t>(max_tiles, sm_count());   // units <= tiles
     bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     DT_CUDA_TRY(cudaFreeAsync(qpop, s));

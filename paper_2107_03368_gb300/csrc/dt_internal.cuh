@@ -201,19 +201,22 @@ int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects
                     const uint64_t *qdesc, const int64_t *qoffsets, int nq, int64_t total,
                     int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
                     int64_t *consumed, int engine, cudaStream_t s);
-// Work unit of the tensor-core scan in list mode: the query tile a_tile
-// (TM rows, the first nvalid of them real) against database rows
-// [row0, row1).  Results go to partial[(a_tile * TM + row) * 2 + half][k].
+// Work unit of the tensor-core scan in list mode: the query tiles a_tile0
+// and a_tile1 (TM rows each, the first nvalid0 / nvalid1 of them real;
+// a_tile1 < 0: none) against database rows [row0, row1).  Results go to
+// partial[a_tile * TM + row][k].
 struct TcUnit {
     int64_t row0, row1;
-    int32_t a_tile, nvalid;
+    int32_t a_tile0, a_tile1, nvalid0, nvalid1;
 };
 // Tensor-core scan over a unit table built on the device: *n_units units
-// (at most max_units); the row r of tile t is query slot_q[t * TM + r]
-// (negative = padding).  Rows are reported through idx_map.
+// covering *n_tiles query tiles (at most max_tiles); the row r of tile t is
+// query slot_q[t * TM + r] (negative = padding).  Rows are reported through
+// idx_map.
 int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
                     const int32_t *slot_q, const TcUnit *units, const int64_t *n_units,
-                    int64_t max_units, int k, uint64_t *partial, cudaStream_t s);
+                    const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
+                    cudaStream_t s);
 constexpr int kTcTileM = 128;
 // Exact top-1 of each query over db on the tensor cores; reported indices go
 // through idx_map when given (ties are broken on the reported index).

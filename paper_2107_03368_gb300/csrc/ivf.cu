@@ -307,39 +307,50 @@ __global__ void pair_count_kernel(const int32_t *__restrict__ probe, int64_t pai
     for (; i < pairs; i += stride) atomicAdd(&counts[probe[i]], 1);
 }
 
-// One block: per list, ceil(count / 128) units, numbered list by list.
+// One block: per list, ceil(count / 128) query tiles (numbered list by
+// list from tile_base) and ceil(tiles / 2) units of up to two tiles each.
 __global__ void unit_plan_kernel(const int32_t *__restrict__ counts, int K,
-                                 const int64_t *__restrict__ offsets, int64_t *__restrict__ unit_base,
-                                 TcUnit *__restrict__ units, int64_t *__restrict__ n_units)
+                                 const int64_t *__restrict__ offsets, int64_t *__restrict__ tile_base,
+                                 TcUnit *__restrict__ units, int64_t *__restrict__ n_units,
+                                 int64_t *__restrict__ n_tiles)
 {
     __shared__ uint32_t tmp[33];
-    uint32_t run = 0;
+    uint32_t run_t = 0, run_u = 0;
     for (int c0 = 0; c0 < K; c0 += blockDim.x) {
         const int c = c0 + threadIdx.x;
         const uint32_t cnt = c < K ? (uint32_t)counts[c] : 0u;
-        const uint32_t nu = (cnt + kTcTileM - 1) / kTcTileM;
-        uint32_t total;
-        const uint32_t before = block_excl_scan(nu, tmp, &total);
+        const uint32_t nt = (cnt + kTcTileM - 1) / kTcTileM;
+        const uint32_t nu = (nt + 1) / 2;
+        uint32_t tot_t, tot_u;
+        const uint32_t bt = block_excl_scan(nt, tmp, &tot_t);
+        const uint32_t bu = block_excl_scan(nu, tmp, &tot_u);
         if (c < K) {
-            const int64_t b = (int64_t)run + before;
-            unit_base[c] = b;
+            const int64_t t0 = (int64_t)run_t + bt, u0 = (int64_t)run_u + bu;
+            tile_base[c] = t0;
             for (uint32_t i = 0; i < nu; ++i) {
                 TcUnit u;
                 u.row0 = offsets[c];
                 u.row1 = offsets[c + 1];
-                u.a_tile = (int32_t)(b + i);
-                u.nvalid = (int32_t)min(cnt - i * kTcTileM, (uint32_t)kTcTileM);
-                units[b + i] = u;
+                u.a_tile0 = (int32_t)(t0 + 2 * i);
+                u.nvalid0 = (int32_t)min(cnt - 2 * i * kTcTileM, (uint32_t)kTcTileM);
+                const bool two = 2 * i + 1 < nt;
+                u.a_tile1 = two ? (int32_t)(t0 + 2 * i + 1) : -1;
+                u.nvalid1 = two ? (int32_t)min(cnt - (2 * i + 1) * kTcTileM, (uint32_t)kTcTileM) : 0;
+                units[u0 + i] = u;
             }
         }
-        run += total;
+        run_t += tot_t;
+        run_u += tot_u;
     }
-    if (threadIdx.x == 0) *n_units = run;
+    if (threadIdx.x == 0) {
+        *n_units = run_u;
+        *n_tiles = run_t;
+    }
 }
 
-// Pair (q, p) -> a row of one of its list's units.
+// Pair (q, p) -> a row of one of its list's query tiles.
 __global__ void pair_scatter_kernel(const int32_t *__restrict__ probe, int64_t nq, int n_probe,
-                                    const int64_t *__restrict__ unit_base, int32_t *__restrict__ fill,
+                                    const int64_t *__restrict__ tile_base, int32_t *__restrict__ fill,
                                     int32_t *__restrict__ slot_q, int64_t *__restrict__ slot_of)
 {
     const int64_t pairs = nq * n_probe;
@@ -348,14 +359,13 @@ __global__ void pair_scatter_kernel(const int32_t *__restrict__ probe, int64_t n
     for (; i < pairs; i += stride) {
         const int c = probe[i];
         const int r = atomicAdd(&fill[c], 1);
-        const int64_t slot = (unit_base[c] + r / kTcTileM) * kTcTileM + r % kTcTileM;
+        const int64_t slot = (tile_base[c] + r / kTcTileM) * kTcTileM + r % kTcTileM;
         slot_q[slot] = (int32_t)(i / n_probe);
         slot_of[i] = slot;
     }
 }
 
-// One warp per query: merge the two column-half lists of each of its
-// pairs; write idx and score.
+// One warp per query: merge the lists of its pairs; write idx and score.
 __global__ void pair_merge_kernel(const uint64_t *__restrict__ partial,
                                   const int64_t *__restrict__ slot_of, int n_probe,
                                   const uint64_t *__restrict__ qs, int64_t nq, int k,
@@ -367,10 +377,8 @@ __global__ void pair_merge_kernel(const uint64_t *__restrict__ partial,
     uint64_t slot = kEmpty;
     for (int p = 0; p < n_probe; ++p) {
         const int64_t sl = slot_of[q * n_probe + p];
-        for (int h = 0; h < 2; ++h) {
-            const uint64_t c = lane < k ? partial[(sl * 2 + h) * k + lane] : kEmpty;
-            warp_list_merge(slot, c, k, lane);
-        }
+        const uint64_t c = lane < k ? partial[sl * k + lane] : kEmpty;
+        warp_list_merge(slot, c, k, lane);
     }
     const uint4 qv = __ldg(reinterpret_cast<const uint4 *>(qs + q * kWords) + lane);
     const QueryWeights w = query_weights(warp_sum(popc4(qv)));
@@ -528,32 +536,35 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     }
     // list-major: probes -> pairs grouped by list -> tensor-core units -> merge
     const int64_t pairs = nq * n_probe;
-    const int64_t max_units = std::min<int64_t>(pairs, (pairs + kTcTileM - 1) / kTcTileM + ix->K);
+    const int64_t max_tiles = std::min<int64_t>(pairs, (pairs + kTcTileM - 1) / kTcTileM + ix->K);
+    const int64_t max_units = max_tiles;
     int32_t *probe = nullptr, *counts = nullptr, *slot_q = nullptr;
-    int64_t *unit_base = nullptr, *n_units = nullptr, *slot_of = nullptr;
+    int64_t *tile_base = nullptr, *n_units = nullptr, *slot_of = nullptr;
     TcUnit *units = nullptr;
     uint64_t *partial = nullptr;
     DT_CUDA_TRY(cudaMallocAsync((void **)&probe, (size_t)pairs * 4, s));
     DT_CUDA_TRY(cudaMallocAsync((void **)&counts, (size_t)ix->K * 4 * 2, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&unit_base, (size_t)ix->K * 8, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&n_units, 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&tile_base, (size_t)ix->K * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&n_units, 16, s));
     DT_CUDA_TRY(cudaMallocAsync((void **)&units, (size_t)max_units * sizeof(TcUnit), s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&slot_q, (size_t)max_units * kTcTileM * 4, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&slot_q, (size_t)max_tiles * kTcTileM * 4, s));
     DT_CUDA_TRY(cudaMallocAsync((void **)&slot_of, (size_t)pairs * 8, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)max_units * kTcTileM * 2 * k * 8, s));
+    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)max_tiles * kTcTileM * k * 8, s));
     int32_t *fill = counts + ix->K;
+    int64_t *n_tiles = n_units + 1;
     DT_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ix->K * 4 * 2, s));
-    DT_CUDA_TRY(cudaMemsetAsync(slot_q, 0xFF, (size_t)max_units * kTcTileM * 4, s));
+    DT_CUDA_TRY(cudaMemsetAsync(slot_q, 0xFF, (size_t)max_tiles * kTcTileM * 4, s));
     ivf_search_kernel<<<(unsigned)nq, ST, smem, s>>>(qemb, d_q, nq, ix->cent_t, ix->K, ix->offsets,
                                                      ix->db, ix->ids, n_probe, k, d_idx, d_score,
                                                      nullptr, d_scanned, probe);
     const unsigned pb = (unsigned)std::min<int64_t>((pairs + 255) / 256, 8192);
     pair_count_kernel<<<pb, 256, 0, s>>>(probe, pairs, counts);
-    unit_plan_kernel<<<1, 1024, 0, s>>>(counts, ix->K, ix->offsets, unit_base, units, n_units);
-    pair_scatter_kernel<<<pb, 256, 0, s>>>(probe, nq, n_probe, unit_base, fill, slot_q, slot_of);
+    unit_plan_kernel<<<1, 1024, 0, s>>>(counts, ix->K, ix->offsets, tile_base, units, n_units,
+                                        n_tiles);
+    pair_scatter_kernel<<<pb, 256, 0, s>>>(probe, nq, n_probe, tile_base, fill, slot_q, slot_of);
     DT_CUDA_TRY(cudaGetLastError());
-    int rc = launch_tc_units(ix->db, ix->n, ix->ids, d_q, slot_q, units, n_units, max_units, k,
-                             partial, s);
+    int rc = launch_tc_units(ix->db, ix->n, ix->ids, d_q, slot_q, units, n_units, n_tiles,
+                             max_tiles, k, partial, s);
     if (rc == DT_OK) {
         pair_merge_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(partial, slot_of, n_probe, d_q,
                                                                    nq, k, d_idx, d_score);
@@ -564,7 +575,7 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     cudaFreeAsync(slot_q, s);
     cudaFreeAsync(units, s);
     cudaFreeAsync(n_units, s);
-    cudaFreeAsync(unit_base, s);
+    cudaFreeAsync(tile_base, s);
     cudaFreeAsync(counts, s);
     cudaFreeAsync(probe, s);
     DT_CUDA_TRY(cudaFreeAsync(qemb, s));
