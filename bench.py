@@ -99,6 +99,23 @@ class Dist:
             self.pg.destroy_process_group()
 
 
+class nvtx:
+    """A named NVTX range around a timed call (lets a profiler capture
+    exactly that call; free when no profiler is attached)."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        import torch
+        torch.cuda.nvtx.range_push(self.name)
+
+    def __exit__(self, *exc):
+        import torch
+        torch.cuda.nvtx.range_pop()
+        return False
+
+
 def aggregate(per_rank_ms, units_per_rank, world):
     """Whole-job throughput: all ranks' units over the slowest rank's time."""
     return units_per_rank * world / (per_rank_ms / 1000.0)
@@ -307,7 +324,8 @@ def run_ours(a, dist):
     sampler.start()
     for i in range(a.steps):
         starts[i].record(stream)
-        step()
+        with nvtx("tree_step"):
+            step()
         ends[i].record(stream)
     torch.cuda.synchronize()
     dist.barrier()
@@ -429,8 +447,9 @@ def time_bf(dt, d_db, d_q, k, path, steps, stream, ref_idx):
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
     s.record(stream)
-    for _ in range(steps):
-        dt.bf_search(d_db, d_q, k, out=out, path=path)
+    with nvtx("bf_path%d" % path):
+        for _ in range(steps):
+            dt.bf_search(d_db, d_q, k, out=out, path=path)
     e.record(stream)
     torch.cuda.synchronize()
     return s.elapsed_time(e) / steps, bool(torch.equal(out[0], ref_idx))
@@ -487,8 +506,9 @@ def learned_leg(a, dist, d_db, d_q, db, tree_qps, bf_qps, stream, ix, tree_idx):
         s = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        for _ in range(reps):
-            idx, _, scanned = ivf.search(d_q, 1, probe, with_scanned=True)
+        with nvtx("learned_search_p%d" % probe):
+            for _ in range(reps):
+                idx, _, scanned = ivf.search(d_q, 1, probe, with_scanned=True)
         e.record(stream)
         torch.cuda.synchronize()
         rec = float((idx[:, 0] == exact).float().mean().item())
@@ -583,8 +603,9 @@ def votes_leg(a, dev, stream, nt):
         torch.cuda.synchronize()
         return s.elapsed_time(e), r
 
-    ms, (votes, winner, consumed) = timed(lambda: dt.retrieve_objects(
-        ix, d_obj, n_obj, d_qd, d_off, 10, seed, engine=2))
+    with nvtx("votes_t10"):
+        ms, (votes, winner, consumed) = timed(lambda: dt.retrieve_objects(
+            ix, d_obj, n_obj, d_qd, d_off, 10, seed, engine=2))
     w = winner.cpu().numpy()
     out["threshold_10"] = {
         "engine": "tensor rounds", "ms": ms, "partial_queries_per_s": a.votes_queries / (ms / 1e3),
