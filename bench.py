@@ -58,6 +58,11 @@ def parse_args(argv=None):
     p.add_argument("--target-recall", type=float, default=0.99)
     p.add_argument("--untrained-baseline", type=int, default=1,
                    help="also sweep the encoder at its initial weights (1/0)")
+    p.add_argument("--workload", choices=["tree", "tensor-bf"], default="tree",
+                   help="tree: the tree-search step (default); tensor-bf: the large-batch "
+                        "brute force, 65,536 queries x 20,000,000 descriptors")
+    p.add_argument("--tc-n", type=int, default=20_000_000)
+    p.add_argument("--tc-nq", type=int, default=65_536)
     return p.parse_args(argv)
 
 
@@ -359,6 +364,10 @@ def run_ours(a, dist):
     e2e_ms = dist.max(e_s.elapsed_time(e_e) / a.steps)
     e2e_value = aggregate(e2e_ms, a.nq, dist.world)
 
+    # the same step captured once in a CUDA graph and replayed
+    graph = graph_replay_leg(lambda: dt.dt_search(ix, d_q, k, out=out), out[0], tree_idx,
+                             stream)
+
     # GPU brute force on the same batch (the method's sequential search), both
     # kernels: popcount (path 1) and the tcgen05 overlap contraction (path 2)
     bf = {}
@@ -400,6 +409,7 @@ def run_ours(a, dist):
         "bf_search": bf,
         "tree_vs_bf_speedup": value / dist.world / bf_best,
         "build_s": build_s,
+        "graph_replay": graph,
         "gpu_traversal_per_query": {kk: v / a.nq for kk, v in gst.items()},
     }
 
@@ -434,6 +444,34 @@ def run_ours(a, dist):
         print(json.dumps(line), flush=True)
     ix.free()
     return 0
+
+
+def graph_replay_leg(fn, result, ref, stream):
+    """Capture fn (stream-ordered, scratch from the stream-ordered allocator)
+    in a CUDA graph, replay it, and time one replay against the direct call's
+    result."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        fn()
+    result.fill_(-1)
+    torch.cuda.synchronize()
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    with nvtx("graph_replay"):
+        g.replay()
+    e.record(stream)
+    torch.cuda.synchronize()
+    same = bool(torch.equal(result, ref))
+    del g
+    return {"ms": s.elapsed_time(e), "same_indices_as_direct": same}
 
 
 def time_bf(dt, d_db, d_q, k, path, steps, stream, ref_idx):
@@ -623,6 +661,101 @@ def votes_leg(a, dev, stream, nt):
     return out
 
 
+def run_tensor_workload(a, dist):
+    """Large-batch brute force: every query against every descriptor on the
+    tensor cores (bf_search path 2), the popcount kernel timed on a sample,
+    both checked against each other and, on a few queries, the oracle."""
+    import torch
+    import oracle
+    from paper_2107_03368_gb300 import dt, synth
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    stream = torch.cuda.current_stream(dev)
+    nt = cpu_cores()
+    seed = SEED + 2                              # the tensor workload's own seed
+    n, nq, k = a.tc_n, a.tc_nq, a.k
+    db, _ = synth.database(seed, n, per_object=a.per_object, nthreads=nt)
+    q, _ = synth.queries(seed + 1000 * dist.rank, db, nq, nthreads=nt)
+    d_db = torch.from_numpy(db.view(np.int64)).to(dev)
+    d_q = torch.from_numpy(q.view(np.int64)).to(dev)
+    out = (torch.empty((nq, k), dtype=torch.int32, device=dev),
+           torch.empty((nq, k), dtype=torch.float32, device=dev), None)
+
+    def step():
+        dt.bf_search(d_db, d_q, k, out=out, path=2)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dist.local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for i in range(a.steps):
+        starts[i].record(stream)
+        with nvtx("bf_path2_large"):
+            step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    dt.dt_sync_status()
+    ms = dist.max(sum(st.elapsed_time(e) for st, e in zip(starts, ends)) / a.steps)
+    value = aggregate(ms, nq, dist.world)
+
+    # popcount kernel on a sample of the queries; same indices as the tensor kernel
+    m = min(2048, nq)
+    p_out = (torch.empty((m, k), dtype=torch.int32, device=dev),
+             torch.empty((m, k), dtype=torch.float32, device=dev), None)
+    dt.bf_search(d_db, d_q[:m], k, out=p_out, path=1)
+    torch.cuda.synchronize()
+    ps = torch.cuda.Event(enable_timing=True)
+    pe = torch.cuda.Event(enable_timing=True)
+    ps.record(stream)
+    dt.bf_search(d_db, d_q[:m], k, out=p_out, path=1)
+    pe.record(stream)
+    torch.cuda.synchronize()
+    popc_ms = ps.elapsed_time(pe)
+    same_popc = bool(torch.equal(p_out[0], out[0][:m]))
+
+    pk = peaks()
+    tf = 2.0 * nq * n * 4096 / (ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": dist.world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "e4m3", "data": "synthetic",
+        "config": {"workload": "tensor-core brute force, %d descriptors x %d queries, top-%d"
+                               % (n, nq, k), "n_db": n, "n_queries": nq, "k": k,
+                   "l2": "inputs larger than L2 (%.2f GB database)" % (n * 512 / 1e9)},
+        "gpu_launches": 3 * a.steps,
+        "clocks": clocks,
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": 2.0 * pk["bf16_tflops"],
+                     "unit": "TFLOP/s", "frac": tf / (2.0 * pk["bf16_tflops"]), "traffic": None,
+                     "peak_kind": "FP8 = 2 x %s bf16 (nominal ratio)" % pk["kind"]},
+        "popc_sample": {"queries": m, "ms": popc_ms, "queries_per_s": m / (popc_ms / 1e3),
+                        "same_indices_as_tensor": same_popc},
+    }
+    if dist.rank == 0 and not a.no_cpu_baseline:
+        sample = 4
+        t0 = time.perf_counter()
+        o_idx, o_score, _ = oracle.bf_topk(db, q[:sample], k, nthreads=nt)
+        cpu_s = time.perf_counter() - t0
+        g_idx = out[0][:sample].cpu().numpy().view(np.uint32).astype(np.int64)
+        g_score = out[1][:sample].cpu().numpy().astype(np.float64)
+        line["oracle_check"] = {
+            "queries": sample, "same_indices": bool(np.array_equal(g_idx, o_idx)),
+            "max_score_rel_err": float(np.max(np.abs(g_score - o_score) / np.maximum(o_score, 1e-300)))}
+        line["cpu_baseline"] = {"value": sample / cpu_s, "unit": "queries/s", "cores": nt,
+                                "kind": "oracle",
+                                "sample": "%d of the %d queries, oracle brute force" % (sample, nq)}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     a = parse_args(argv)
     if a.impl == "reference":
@@ -637,6 +770,8 @@ def main(argv=None):
         return 1
     dist = Dist("nccl")
     try:
+        if a.workload == "tensor-bf":
+            return run_tensor_workload(a, dist)
         return run_ours(a, dist)
     finally:
         dist.close()

@@ -2,7 +2,8 @@
 the tensor cores (tcgen05, FP32 accumulation in tensor memory) — against the
 oracle (indices and (A, B) counts bit-exact, scores within 1e-6 relative)
 and against the popcount path (identical outputs), at sizes that leave
-ragged 128-query and 256-descriptor tiles."""
+ragged 128-query and 128-descriptor tiles, and units whose second query
+tile is absent (an odd number of query tiles)."""
 import numpy as np
 import pytest
 import torch
@@ -14,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("n,nq,k", [(1, 1, 1), (5, 3, 10), (256, 128, 1), (257, 129, 10),
-                                    (1000, 130, 32), (4099, 7, 5), (20000, 300, 10)])
+                                    (1000, 130, 32), (4099, 7, 5), (20000, 300, 10),
+                                    (300, 257, 3), (128, 385, 7), (129, 640, 1)])
 def test_tc_matches_oracle(n, nq, k):
     db = mixed_db(n + 11, n)
     q = edge_queries(n + 12, db, nq)
