@@ -298,9 +298,13 @@ int enc_get_params(const dt_encoder *enc, float *h_params);  /* host [enc_param_
 int enc_set_params(dt_encoder *enc, const float *h_params);
 int enc_get_grads(const dt_encoder *enc, float *h_grads);    /* gradient of the last train step */
 /* Embeddings of n descriptors into d_out_bf16 [n][128] (BF16 bits) and/or
- * d_out_f32 [n][128]; at least one output.  Stream-ordered. */
+ * d_out_f32 [n][128]; at least one output.  Stream-ordered.
+ * path: 1 = FP32 arithmetic on CUDA cores (one fused kernel); 2 = tensor
+ * cores, the convolutions and dense layers as GEMMs with BF16 operands and
+ * FP32 accumulation (agrees with path 1 to about 1e-2); 0 = 2 for
+ * n >= 4096, else 1.  The inverted file uses path 0. */
 int enc_embed(const dt_encoder *enc, const uint64_t *d_bits, int64_t n, uint16_t *d_out_bf16,
-              float *d_out_f32, void *stream);
+              float *d_out_f32, int32_t path, void *stream);
 /* One step of InfoNCE with in-batch negatives on B (query, target) pairs,
  * L = mean_i [ log sum_j exp(<e_qi, e_tj>/tau) - <e_qi, e_ti>/tau ], then Adam
  * (beta 0.9 / 0.999, eps 1e-8) with learning rate lr unless update = 0.

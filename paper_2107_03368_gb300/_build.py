@@ -29,6 +29,7 @@ CUDA_SOURCES = [
     "dt_build.cu",
     "dt_search.cu",
     "encoder.cu",
+    "enc_tc.cu",
     "ivf.cu",
     "votes.cu",
 ]

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "dt_internal.cuh"
+#include "encoder_layout.cuh"
 
 namespace dtk {
 
@@ -247,12 +248,13 @@ int dt_sync_status(void *stream)
 {
     g_last_error.clear();
     DT_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
-    bool raised = false, raised_tc = false;
+    bool raised = false, raised_tc = false, raised_enc = false;
     if (int r = take_bf_error(&raised)) return r;
     if (int r = take_tc_error(&raised_tc)) return r;
-    raised = raised || raised_tc;
+    if (int r = take_enc_tc_error(&raised_enc)) return r;
+    raised = raised || raised_tc || raised_enc;
     if (raised) {
-        set_error("a database tile copy did not arrive within the spin limit");
+        set_error("a tile copy or tensor-core stage did not arrive within the spin limit");
         return DT_ETIMEOUT;
     }
     return DT_OK;

@@ -17,7 +17,9 @@
 // s_ij = <e_q[i], e_t[j]> / tau, is differentiated by hand back through
 // every layer; Adam updates the parameters.  Kernels are plain FP32 on CUDA
 // cores, one thread per output element (weight gradients split over the
-// batch with atomics).  Inference (enc_embed) is one fused kernel over
+// batch with atomics).  Inference (enc_embed) runs on the tensor cores for
+// large batches (enc_tc.cu, BF16 operands); the FP32 inference path here is
+// one fused kernel over
 // weights re-laid out output-channel-contiguous: each thread keeps all
 // output channels of its position in registers (conv2: 64, conv3: 16), a
 // CTA keeps an image's conv activations in shared memory and runs the two
@@ -30,17 +32,12 @@
 #include <cuda_bf16.h>
 
 #include "dt_internal.cuh"
+#include "encoder_layout.cuh"
 
 namespace dtk {
 namespace {
 
-constexpr int C1 = 32, C2 = 64, C3 = 64, H1 = 32, H2 = 16, H3 = 8, HP = 4;
-constexpr int F0 = C3 * HP * HP, F1 = 256, F2 = 128;
-constexpr int64_t OW1 = 0, OB1 = OW1 + C1 * 9, OW2 = OB1 + C1, OB2 = OW2 + C2 * C1 * 9,
-                  OW3 = OB2 + C2, OB3 = OW3 + C3 * C2 * 9, OWF1 = OB3 + C3, OBF1 = OWF1 + F1 * F0,
-                  OWF2 = OBF1 + F1, OBF2 = OWF2 + F2 * F1, NPARAM = OBF2 + F2;
-static_assert(NPARAM == 351040, "parameter count");
-constexpr int A1 = C1 * H1 * H1, A2 = C2 * H2 * H2, A3 = C3 * H3 * H3;
+using namespace enc;
 
 __device__ __forceinline__ float bit_px(const uint64_t *img, int r, int c)
 {
@@ -714,11 +711,15 @@ int enc_get_grads(const dt_encoder *e, float *h_grads)
 }
 
 int enc_embed(const dt_encoder *e, const uint64_t *d_bits, int64_t n, uint16_t *d_out_bf16,
-              float *d_out_f32, void *stream)
+              float *d_out_f32, int32_t path, void *stream)
 {
     DT_CHECK_ARG(e && d_bits && n >= 0 && (d_out_bf16 || d_out_f32), "bad arguments");
+    DT_CHECK_ARG(path >= 0 && path <= 2, "path must be 0, 1 or 2");
     if (n == 0) return DT_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (path == 2 || (path == 0 && n >= 4096))
+        return launch_embed_tc(e->P, d_bits, n, reinterpret_cast<__nv_bfloat16 *>(d_out_bf16),
+                               d_out_f32, s);
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {

@@ -25,7 +25,7 @@
 
 struct dt_encoder;
 extern "C" int enc_embed(const dt_encoder *e, const uint64_t *d_bits, int64_t n, uint16_t *d_out_bf16,
-                         float *d_out_f32, void *stream);
+                         float *d_out_f32, int32_t path, void *stream);
 
 namespace dtk {
 namespace {
@@ -453,7 +453,7 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
         set_error("ivf_build: allocation failed");
         rc = DT_ENOMEM;
     }
-    if (rc == DT_OK) rc = enc_embed(enc, d_db, n, reinterpret_cast<uint16_t *>(emb), nullptr, s);
+    if (rc == DT_OK) rc = enc_embed(enc, d_db, n, reinterpret_cast<uint16_t *>(emb), nullptr, 0, s);
     if (rc == DT_OK) {
         init_centroids_kernel<<<(unsigned)(((int64_t)K * D + 255) / 256), 256, 0, s>>>(emb, n, K, ix->cent);
         const unsigned ablocks = (unsigned)((n + KT - 1) / KT);
@@ -521,7 +521,7 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     const bool tensor = path == 2 || (path == 0 && nq >= kTcTileM);
     float *qemb = nullptr;
     DT_CUDA_TRY(cudaMallocAsync((void **)&qemb, (size_t)nq * D * 4, s));
-    if (int r = enc_embed(enc, d_q, nq, nullptr, qemb, s)) return r;
+    if (int r = enc_embed(enc, d_q, nq, nullptr, qemb, 0, s)) return r;
     const size_t smem = (size_t)ix->K * 4;
     if (smem > 48 * 1024)
         DT_CUDA_TRY(cudaFuncSetAttribute(ivf_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

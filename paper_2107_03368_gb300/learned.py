@@ -31,7 +31,7 @@ def _lib():
             "enc_get_params": ([P, P], ctypes.c_int),
             "enc_set_params": ([P, P], ctypes.c_int),
             "enc_get_grads": ([P, P], ctypes.c_int),
-            "enc_embed": ([P, P, i64, P, P, P], ctypes.c_int),
+            "enc_embed": ([P, P, i64, P, P, i32, P], ctypes.c_int),
             "enc_train_step": ([P, P, P, i32, f32, f32, i32, P, P], ctypes.c_int),
             "ivf_build": ([P, P, i64, i32, i32, P, P], ctypes.c_int),
             "ivf_free": ([P], None),
@@ -76,16 +76,17 @@ class Encoder:
         dt._check(_lib().enc_get_grads(self._h, ctypes.c_void_p(out.ctypes.data)), "enc_get_grads")
         return out
 
-    def embed(self, bits, bf16=False, stream=None):
+    def embed(self, bits, bf16=False, path=0, stream=None):
+        """path: 0 auto, 1 FP32 on CUDA cores, 2 tensor cores (BF16 operands)."""
         bits = dt._desc(bits, "bits")
         n = bits.shape[0]
         if bf16:
             out = torch.empty((n, 128), dtype=torch.int16, device=bits.device)
-            dt._check(_lib().enc_embed(self._h, _p(bits), n, _p(out), None, dt._stream(stream)),
-                      "enc_embed")
+            dt._check(_lib().enc_embed(self._h, _p(bits), n, _p(out), None, path,
+                                       dt._stream(stream)), "enc_embed")
             return out.view(torch.bfloat16)
         out = torch.empty((n, 128), dtype=torch.float32, device=bits.device)
-        dt._check(_lib().enc_embed(self._h, _p(bits), n, None, _p(out), dt._stream(stream)),
+        dt._check(_lib().enc_embed(self._h, _p(bits), n, None, _p(out), path, dt._stream(stream)),
                   "enc_embed")
         return out
 
