@@ -31,6 +31,9 @@
  * Memory: every pointer named d_* is CUDA device memory owned by the caller
  *   and must stay valid until the stream reaches the call's end.  The
  *   library owns dt_index objects and any scratch space it allocates.
+ *   Scratch comes from the device's default stream-ordered memory pool;
+ *   on first use of a device the library raises that pool's release
+ *   threshold to 16 GiB, so freed scratch stays cached between calls.
  * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
  *   enqueue their work and return; outputs are ready when the stream is.
  *   dt_build and calls that return host statistics synchronise the stream.
@@ -327,7 +330,8 @@ int ivf_offsets(const dt_ivf *ivf, int64_t *h_offsets);      /* host [n_lists + 
  * path: 1 = one thread block per query scanning its lists on CUDA cores;
  * 2 = the (query, list) pairs regrouped by list, each list's rows scanned
  * once for all its queries on the tensor cores (as bf_search path 2);
- * 0 = 2 for nq >= 128, else 1.  Both give the same results. */
+ * 0 = 2 when nq * n_probe >= 10 * n_lists (about ten queries per list),
+ * else 1.  Both give the same results. */
 int ivf_search(const dt_ivf *ivf, const dt_encoder *enc, const uint64_t *d_q, int64_t nq, int32_t k,
                int32_t n_probe, uint32_t *d_idx, float *d_score, int64_t *d_scanned, int32_t path,
                void *stream);

@@ -23,6 +23,16 @@ int sm_count()
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         cached[dev] = v > 0 ? v : 1;
+        // Scratch comes from the stream-ordered allocator; by default its
+        // pool hands freed memory back to the system at every
+        // synchronisation, so the next call maps it again.  Keep up to
+        // 16 GiB cached in the device's default pool instead.
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = 16ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
     }
     return cached[dev];
 }

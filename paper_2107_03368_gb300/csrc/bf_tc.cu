@@ -157,8 +157,9 @@ __global__ void widen_queries_kernel(const uint64_t *__restrict__ q, int64_t nq,
     }
 }
 
-// Gathered query tiles: row r of tile mt is query slot_q[mt * TM + r]
-// (negative: a zero row); tiles at or beyond *n_tiles are left alone.
+// Gathered query tiles: row r of tile mt is query slot_q[mt * TM + r];
+// padding rows (negative) are not written (their accumulator rows are
+// never read), nor are tiles at or beyond *n_tiles.
 __global__ void widen_gather_kernel(const uint64_t *__restrict__ q, const int32_t *__restrict__ slot_q,
                                     const int64_t *__restrict__ n_tiles, int64_t max_tiles,
                                     unsigned char *__restrict__ a_exp, uint32_t *__restrict__ qpop)
@@ -170,17 +171,15 @@ __global__ void widen_gather_kernel(const uint64_t *__restrict__ q, const int32_
     const int64_t mt = id / ((int64_t)NCHUNK * TM);
     if (mt >= *n_tiles) return;
     const int32_t qi = slot_q[mt * TM + row];
-    uint4 bits = make_uint4(0, 0, 0, 0);
-    if (qi >= 0) bits = __ldg(reinterpret_cast<const uint4 *>(q + (int64_t)qi * kWords) + c);
+    if (qi < 0) return;
+    const uint4 bits = __ldg(reinterpret_cast<const uint4 *>(q + (int64_t)qi * kWords) + c);
     store_row_chunk(a_exp + ((size_t)mt * NCHUNK + c) * A_STAGE, row, bits);
     if (c == 0) {
         uint32_t s = 0;
-        if (qi >= 0) {
-            const uint4 *r = reinterpret_cast<const uint4 *>(q + (int64_t)qi * kWords);
-            for (int j = 0; j < 32; ++j) {
-                uint4 v = __ldg(r + j);
-                s += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-            }
+        const uint4 *r = reinterpret_cast<const uint4 *>(q + (int64_t)qi * kWords);
+        for (int j = 0; j < 32; ++j) {
+            uint4 v = __ldg(r + j);
+            s += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
         }
         qpop[mt * TM + row] = s;
     }

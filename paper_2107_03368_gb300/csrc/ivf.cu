@@ -197,7 +197,7 @@ ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ q
     __syncthreads();
     for (int c = tid; c < K; c += ST) {       // centroids stored [D][K]: coalesced
         float s = 0.f;
-        for (int d = 0; d < D; ++d) s += qe[d] * __ldg(cent + (int64_t)d * K + c);
+        for (int d = 0; d < D; ++d) s = fmaf(qe[d], __ldg(cent + (int64_t)d * K + c), s);
         csc[c] = s;
     }
     __syncthreads();
@@ -292,6 +292,70 @@ ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ q
         if (lane == 0 && scanned) scanned[q] = rows;
     }
     (void)ab;
+}
+
+// Probes only, QB queries per block: every centroid load feeds QB dot
+// products (the scores and the choice are those of ivf_search_kernel).
+template <int QB>
+__global__ void __launch_bounds__(ST)
+ivf_probe_kernel(const float *__restrict__ qemb, int64_t nq, const float *__restrict__ cent, int K,
+                 const int64_t *__restrict__ offsets, int n_probe, int32_t *__restrict__ probe_out,
+                 int64_t *__restrict__ scanned)
+{
+    extern __shared__ float csc[];                   // [QB][K]
+    __shared__ float qe[QB][D];
+    __shared__ unsigned long long red[ST / 32];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t q0 = (int64_t)blockIdx.x * QB;
+    for (int i = tid; i < QB * D; i += ST) {
+        const int64_t q = q0 + i / D;
+        qe[i / D][i % D] = q < nq ? qemb[q * D + i % D] : 0.f;
+    }
+    __syncthreads();
+    for (int c = tid; c < K; c += ST) {
+        float sc[QB];
+#pragma unroll
+        for (int i = 0; i < QB; ++i) sc[i] = 0.f;
+        for (int d = 0; d < D; ++d) {
+            const float w = __ldg(cent + (int64_t)d * K + c);
+#pragma unroll
+            for (int i = 0; i < QB; ++i) sc[i] = fmaf(qe[i][d], w, sc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < QB; ++i) csc[i * K + c] = sc[i];
+    }
+    __syncthreads();
+    for (int i = 0; i < QB; ++i) {
+        const int64_t q = q0 + i;
+        if (q >= nq) break;                          // uniform across the block
+        float *sc = csc + (int64_t)i * K;
+        int64_t rows = 0;
+        for (int p = 0; p < n_probe; ++p) {
+            unsigned long long b = 0ull;
+            for (int c = tid; c < K; c += ST) {
+                uint32_t fb = __float_as_uint(sc[c]);
+                fb = (fb & 0x80000000u) ? ~fb : (fb | 0x80000000u);
+                const unsigned long long key = ((unsigned long long)fb << 32) | (0xFFFFFFFFu - (uint32_t)c);
+                b = key > b ? key : b;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
+                b = u > b ? u : b;
+            }
+            if (lane == 0) red[wid] = b;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long m = 0ull;
+                for (int w = 0; w < ST / 32; ++w) m = red[w] > m ? red[w] : m;
+                const int c = (int)(0xFFFFFFFFu - (uint32_t)(m & 0xFFFFFFFFu));
+                probe_out[q * n_probe + p] = c;
+                rows += offsets[c + 1] - offsets[c];
+                sc[c] = -INFINITY;
+            }
+            __syncthreads();
+        }
+        if (tid == 0 && scanned) scanned[q] = rows;
+    }
 }
 
 // ------------------------------------------------ list-major search on the tensor cores
@@ -518,7 +582,9 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     DT_CHECK_ARG(nq <= (1LL << 31) / MAX_PROBE, "nq out of range");
     if (nq == 0) return DT_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool tensor = path == 2 || (path == 0 && nq >= kTcTileM);
+    // the list-major scan multiplies whole 128-query tiles: worth it from
+    // about 10 queries per list on average (measured crossover)
+    const bool tensor = path == 2 || (path == 0 && nq * n_probe >= 10LL * ix->K);
     float *qemb = nullptr;
     DT_CUDA_TRY(cudaMallocAsync((void **)&qemb, (size_t)nq * D * 4, s));
     if (int r = enc_embed(enc, d_q, nq, nullptr, qemb, 0, s)) return r;
@@ -554,9 +620,16 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     int64_t *n_tiles = n_units + 1;
     DT_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ix->K * 4 * 2, s));
     DT_CUDA_TRY(cudaMemsetAsync(slot_q, 0xFF, (size_t)max_tiles * kTcTileM * 4, s));
-    ivf_search_kernel<<<(unsigned)nq, ST, smem, s>>>(qemb, d_q, nq, ix->cent_t, ix->K, ix->offsets,
-                                                     ix->db, ix->ids, n_probe, k, d_idx, d_score,
-                                                     nullptr, d_scanned, probe);
+    {   // probes: as many queries per block as the scores of four fit in shared memory
+        const int qb = (size_t)ix->K * 4 * 4 <= 200 * 1024 ? 4 : (size_t)ix->K * 4 * 2 <= 200 * 1024 ? 2 : 1;
+        const size_t psmem = (size_t)qb * ix->K * 4;
+        auto kern = qb == 4 ? ivf_probe_kernel<4> : qb == 2 ? ivf_probe_kernel<2> : ivf_probe_kernel<1>;
+        if (psmem > 48 * 1024)
+            DT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)psmem));
+        kern<<<(unsigned)((nq + qb - 1) / qb), ST, psmem, s>>>(qemb, nq, ix->cent_t, ix->K,
+                                                               ix->offsets, n_probe, probe, d_scanned);
+    }
     const unsigned pb = (unsigned)std::min<int64_t>((pairs + 255) / 256, 8192);
     pair_count_kernel<<<pb, 256, 0, s>>>(probe, pairs, counts);
     unit_plan_kernel<<<1, 1024, 0, s>>>(counts, ix->K, ix->offsets, tile_base, units, n_units,
