@@ -52,7 +52,9 @@ def parse_args(argv=None):
     p.add_argument("--votes-queries", type=int, default=1000)
     p.add_argument("--votes-sample", type=int, default=20,
                    help="partial queries counted in full (threshold 0)")
-    p.add_argument("--train-steps", type=int, default=1500, help="encoder training steps")
+    p.add_argument("--train-steps", type=int, default=4000, help="encoder training steps")
+    p.add_argument("--train-epochs", type=int, default=2,
+                   help="passes over each round of 16,384 (query, exact NN) pairs")
     p.add_argument("--train-batch", type=int, default=256)
     p.add_argument("--n-lists", type=int, default=4096, help="inverted-file lists")
     p.add_argument("--target-recall", type=float, default=0.99)
@@ -530,7 +532,7 @@ def learned_leg(a, dist, d_db, d_q, db, tree_qps, bf_qps, stream, ix, tree_idx):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     hist = learned.train(enc, d_db, make_queries, steps=a.train_steps, batch=a.train_batch,
-                         lr=1e-3, tau=0.05)
+                         lr=1e-3, tau=0.05, epochs_per_round=a.train_epochs)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -554,16 +556,16 @@ def learned_leg(a, dist, d_db, d_q, db, tree_qps, bf_qps, stream, ix, tree_idx):
 
     sweep = []
     chosen = None
-    probe = 1
-    while probe <= a.n_lists:
+    probes = [p for p in (1, 2, 4, 8, 16, 24, 32, 48, 64, 96, 128, 192, 256) if p <= a.n_lists]
+    for probe in probes:
         ms, rec, scanned = run(probe, 1)
         sweep.append({"n_probe": probe, "recall_at_1": rec, "ms": ms,
                       "scanned_per_query": scanned})
         if rec >= a.target_recall:
             chosen = probe
             break
-        probe *= 2
-    out = {"train_steps": a.train_steps, "train_pairs": a.train_steps * a.train_batch,
+    out = {"train_steps": a.train_steps, "train_epochs_per_round": a.train_epochs,
+           "train_pairs": a.train_steps * a.train_batch // a.train_epochs,
            "train_s": train_s, "loss_first": hist[0][1], "loss_last": hist[-1][1],
            "ivf_build_s": build_s, "n_lists": a.n_lists, "sweep": sweep,
            "target_recall_at_1": a.target_recall}

@@ -294,17 +294,19 @@ ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ q
     (void)ab;
 }
 
-// Probes only, QB queries per block: every centroid load feeds QB dot
-// products (the scores and the choice are those of ivf_search_kernel).
+// Probes only, QB queries per block (QB <= 8): every centroid load feeds
+// QB dot products; then warp w chooses query w's n_probe lists from the
+// scores in shared memory by repeated warp-wide argmax (no block
+// barriers).  Scores, order and ties are those of ivf_search_kernel.
 template <int QB>
 __global__ void __launch_bounds__(ST)
 ivf_probe_kernel(const float *__restrict__ qemb, int64_t nq, const float *__restrict__ cent, int K,
                  const int64_t *__restrict__ offsets, int n_probe, int32_t *__restrict__ probe_out,
                  int64_t *__restrict__ scanned)
 {
+    static_assert(QB <= ST / 32, "one warp per query");
     extern __shared__ float csc[];                   // [QB][K]
     __shared__ float qe[QB][D];
-    __shared__ unsigned long long red[ST / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * QB;
     for (int i = tid; i < QB * D; i += ST) {
@@ -325,37 +327,31 @@ ivf_probe_kernel(const float *__restrict__ qemb, int64_t nq, const float *__rest
         for (int i = 0; i < QB; ++i) csc[i * K + c] = sc[i];
     }
     __syncthreads();
-    for (int i = 0; i < QB; ++i) {
-        const int64_t q = q0 + i;
-        if (q >= nq) break;                          // uniform across the block
-        float *sc = csc + (int64_t)i * K;
-        int64_t rows = 0;
-        for (int p = 0; p < n_probe; ++p) {
-            unsigned long long b = 0ull;
-            for (int c = tid; c < K; c += ST) {
-                uint32_t fb = __float_as_uint(sc[c]);
-                fb = (fb & 0x80000000u) ? ~fb : (fb | 0x80000000u);
-                const unsigned long long key = ((unsigned long long)fb << 32) | (0xFFFFFFFFu - (uint32_t)c);
-                b = key > b ? key : b;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
-                b = u > b ? u : b;
-            }
-            if (lane == 0) red[wid] = b;
-            __syncthreads();
-            if (tid == 0) {
-                unsigned long long m = 0ull;
-                for (int w = 0; w < ST / 32; ++w) m = red[w] > m ? red[w] : m;
-                const int c = (int)(0xFFFFFFFFu - (uint32_t)(m & 0xFFFFFFFFu));
-                probe_out[q * n_probe + p] = c;
-                rows += offsets[c + 1] - offsets[c];
-                sc[c] = -INFINITY;
-            }
-            __syncthreads();
+    const int64_t q = q0 + wid;
+    if (wid >= QB || q >= nq) return;
+    float *sc = csc + (int64_t)wid * K;
+    int64_t rows = 0;
+    for (int p = 0; p < n_probe; ++p) {
+        unsigned long long b = 0ull;
+        for (int c = lane; c < K; c += 32) {
+            uint32_t fb = __float_as_uint(sc[c]);
+            fb = (fb & 0x80000000u) ? ~fb : (fb | 0x80000000u);
+            const unsigned long long key = ((unsigned long long)fb << 32) | (0xFFFFFFFFu - (uint32_t)c);
+            b = key > b ? key : b;
         }
-        if (tid == 0 && scanned) scanned[q] = rows;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
+            b = u > b ? u : b;
+        }
+        const int c = (int)(0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFu));
+        if (lane == 0) {
+            probe_out[q * n_probe + p] = c;
+            rows += offsets[c + 1] - offsets[c];
+            sc[c] = -INFINITY;
+        }
+        __syncwarp();
     }
+    if (lane == 0 && scanned) scanned[q] = rows;
 }
 
 // ------------------------------------------------ list-major search on the tensor cores
@@ -620,10 +616,12 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     int64_t *n_tiles = n_units + 1;
     DT_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ix->K * 4 * 2, s));
     DT_CUDA_TRY(cudaMemsetAsync(slot_q, 0xFF, (size_t)max_tiles * kTcTileM * 4, s));
-    {   // probes: as many queries per block as the scores of four fit in shared memory
-        const int qb = (size_t)ix->K * 4 * 4 <= 200 * 1024 ? 4 : (size_t)ix->K * 4 * 2 <= 200 * 1024 ? 2 : 1;
-        const size_t psmem = (size_t)qb * ix->K * 4;
-        auto kern = qb == 4 ? ivf_probe_kernel<4> : qb == 2 ? ivf_probe_kernel<2> : ivf_probe_kernel<1>;
+    {   // probes: up to eight queries per block, as many as their scores fit in shared memory
+        const size_t per_q = (size_t)ix->K * 4, room = 200 * 1024;
+        const int qb = per_q * 8 <= room ? 8 : per_q * 4 <= room ? 4 : per_q * 2 <= room ? 2 : 1;
+        const size_t psmem = (size_t)qb * per_q;
+        auto kern = qb == 8 ? ivf_probe_kernel<8> : qb == 4 ? ivf_probe_kernel<4>
+                  : qb == 2 ? ivf_probe_kernel<2> : ivf_probe_kernel<1>;
         if (psmem > 48 * 1024)
             DT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)psmem));

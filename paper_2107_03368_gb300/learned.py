@@ -152,12 +152,13 @@ class IVF:
 
 
 def train(enc: Encoder, d_db, make_queries, steps, batch=256, lr=1e-3, tau=0.05, log=None,
-          pairs_per_round=8192):
+          epochs_per_round=1):
     """Train on (query, exact nearest neighbour) pairs.
 
     make_queries(round) -> uint64 numpy [m, 64] new query descriptors; their
-    exact nearest neighbours come from bf_search on d_db.  Returns the loss
-    history."""
+    exact nearest neighbours come from bf_search on d_db, and each round's
+    pairs are used for epochs_per_round passes (reshuffled).  Returns the
+    loss history."""
     losses = []
     step = 0
     rnd = 0
@@ -167,17 +168,18 @@ def train(enc: Encoder, d_db, make_queries, steps, batch=256, lr=1e-3, tau=0.05,
         d_q = torch.from_numpy(np.ascontiguousarray(q).view(np.int64)).to(d_db.device)
         nn, _, _ = dt.bf_search(d_db, d_q, 1)
         tgt = d_db[nn[:, 0].long()]
-        perm = torch.randperm(d_q.shape[0], device=d_q.device)
-        for b0 in range(0, d_q.shape[0] - batch + 1, batch):
-            if step >= steps:
-                break
-            sel = perm[b0:b0 + batch]
-            want = (step % 20 == 0) or step == steps - 1
-            loss = enc.train_step(d_q[sel].contiguous(), tgt[sel].contiguous(), lr=lr, tau=tau,
-                                  want_loss=want)
-            if want:
-                losses.append((step, loss))
-                if log:
-                    log(step, loss)
-            step += 1
+        for _ in range(epochs_per_round):
+            perm = torch.randperm(d_q.shape[0], device=d_q.device)
+            for b0 in range(0, d_q.shape[0] - batch + 1, batch):
+                if step >= steps:
+                    break
+                sel = perm[b0:b0 + batch]
+                want = (step % 20 == 0) or step == steps - 1
+                loss = enc.train_step(d_q[sel].contiguous(), tgt[sel].contiguous(), lr=lr,
+                                      tau=tau, want_loss=want)
+                if want:
+                    losses.append((step, loss))
+                    if log:
+                        log(step, loss)
+                step += 1
     return losses
