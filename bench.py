@@ -659,6 +659,17 @@ def votes_leg(a, dev, stream, nt):
     out["threshold_0_sample"] = {
         "engine": "tensor", "partial_queries": m, "query_descriptors": n_desc, "ms": ms0,
         "descriptor_nn_per_s": n_desc / (ms0 / 1e3)}
+    # the same call (all its uneven queries in one call) captured once in a
+    # CUDA graph and replayed
+    vo = (torch.empty((m, n_obj), dtype=torch.int32, device=dev),
+          torch.empty(m, dtype=torch.int32, device=dev),
+          torch.empty(m, dtype=torch.int64, device=dev))
+    q_sub = d_qd[:n_desc]
+    ref_votes, _, _ = dt.retrieve_objects(ix, d_obj, n_obj, q_sub, sub_off, 0, seed, engine=2)
+    torch.cuda.synchronize()
+    out["threshold_0_sample"]["graph_replay"] = graph_replay_leg(
+        lambda: dt.retrieve_objects(ix, d_obj, n_obj, q_sub, sub_off, 0, seed, engine=2, out=vo),
+        vo[0], ref_votes, stream)
     ix.free()
     return out
 

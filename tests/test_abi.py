@@ -59,6 +59,22 @@ def test_bad_sizes_are_rejected():
     assert lib.dt_get_info(None, None) == dt.DT_EINVAL
 
 
+def test_new_entry_points_check_their_arguments_first():
+    """Warm-started search, inverted-file search and embedding reject bad
+    arguments with DT_EINVAL before touching the device."""
+    from paper_2107_03368_gb300 import learned
+    lib = learned._lib()
+    assert lib.dt_search_seeded(None, None, 5, 1, None, 0, None, None, None, None,
+                                None) == dt.DT_EINVAL
+    dummy = ctypes.c_void_p(16)
+    # n_seed out of range, on a non-null (never dereferenced) index handle
+    assert lib.dt_search_seeded(dummy, None, 5, 1, None, 5000, None, None, None, None,
+                                None) == dt.DT_EINVAL
+    assert "n_seed" in dt.dt_last_error()
+    assert lib.ivf_search(None, None, None, 5, 1, 1, None, None, None, 0, None) == dt.DT_EINVAL
+    assert lib.enc_embed(None, None, 5, None, None, 0, None) == dt.DT_EINVAL
+
+
 def test_tune_table_file_roundtrip(tmp_path):
     p = tmp_path / "tune.txt"
     p.write_text("0 23 13 10 152 256 3\n1 23 13 10 152 8 0\nbad line\n")
