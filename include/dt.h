@@ -336,6 +336,20 @@ int ivf_search(const dt_ivf *ivf, const dt_encoder *enc, const uint64_t *d_q, in
                int32_t n_probe, uint32_t *d_idx, float *d_score, int64_t *d_scanned, int32_t path,
                void *stream);
 
+/*
+ * Test hooks for failure handling (the paper has no counterpart; both are
+ * off by default and affect only this process).
+ * dt_debug_fail_allocation(n): the n-th scratch allocation from now on
+ *   reports failure (the call returns DT_ENOMEM); n <= 0 switches it off.
+ * dt_debug_inject_missing_copy(on): while on, popcount brute-force
+ *   launches (bf_search path 1) skip the copy of each thread block's first
+ *   database tile and wait for it only a few thousand polls, so the bounded
+ *   wait gives up: the results are void and dt_sync_status returns
+ *   DT_ETIMEOUT.  Nothing faults, and later calls work normally.
+ */
+void dt_debug_fail_allocation(int32_t nth);
+void dt_debug_inject_missing_copy(int32_t on);
+
 /* Release an index (NULL is allowed).  Synchronises the device it lives on. */
 void dt_free(dt_index *index);
 

@@ -1,5 +1,6 @@
 // api.cu — the C ABI of include/dt.h: argument checks, index lifetime and
 // dispatch to the kernel launchers.  No computation happens here.
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -35,6 +36,21 @@ int sm_count()
         cudaGetLastError();
     }
     return cached[dev];
+}
+
+// Test hook: when positive, the n-th scratch allocation from now fails.
+static std::atomic<int> g_fail_alloc{0};
+
+cudaError_t dt_malloc_async(void **p, size_t bytes, cudaStream_t s)
+{
+    int n = g_fail_alloc.load();
+    while (n > 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {
+    }
+    if (n == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, s);
 }
 
 // A device (or managed) allocation; host pointers would make kernels fault.
@@ -253,6 +269,10 @@ int retrieve_objects(const dt_index *ix, const uint32_t *d_object_of_desc, int32
                            vote_threshold, seed, d_votes, d_winner, d_consumed, engine,
                            (cudaStream_t)stream);
 }
+
+void dt_debug_fail_allocation(int32_t nth) { g_fail_alloc.store(nth > 0 ? nth : 0); }
+
+void dt_debug_inject_missing_copy(int32_t on) { set_drop_copy(on != 0); }
 
 int dt_sync_status(void *stream)
 {

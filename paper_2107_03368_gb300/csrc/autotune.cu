@@ -104,10 +104,11 @@ int dt_autotune(const dt_index *ix, const uint64_t *d_db, int64_t n, const uint6
     DT_CHECK_ARG(k >= 1 && k <= DT_MAX_K, "k must be in [1, DT_MAX_K]");
     DT_CHECK_ARG(ix != nullptr || (d_db != nullptr && n >= 1), "an index or a database is required");
     cudaStream_t s = (cudaStream_t)stream;
+    Scratch scratch(s);
     uint32_t *idx = nullptr;
     float *score = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&idx, (size_t)nq * k * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&score, (size_t)nq * k * 4, s));
+    DT_CUDA_TRY(scratch.alloc(&idx, (size_t)nq * k * 4));
+    DT_CUDA_TRY(scratch.alloc(&score, (size_t)nq * k * 4));
     int tried = 0;
     if (ix) {
         TuneCfg best{0, 0};
@@ -165,8 +166,6 @@ int dt_autotune(const dt_index *ix, const uint64_t *d_db, int64_t n, const uint6
             }
         }
     }
-    cudaFreeAsync(score, s);
-    cudaFreeAsync(idx, s);
     DT_CUDA_TRY(cudaStreamSynchronize(s));
     if (report) report->candidates_timed = tried;
     return DT_OK;

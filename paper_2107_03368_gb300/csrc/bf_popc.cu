@@ -21,6 +21,7 @@
 //     the database is read from HBM about once per split wave.  A second
 //     kernel merges the per-split lists and writes idx / score / (A, B).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -51,7 +52,7 @@ __device__ uint32_t g_bf_error;
 __global__ void __launch_bounds__(THREADS, 2)
 bf_popc_kernel(const uint64_t *__restrict__ db, int64_t n, const uint64_t *__restrict__ qs,
                int64_t nq, int k, int64_t tiles_per_split, uint64_t *__restrict__ partial,
-               uint32_t *err)
+               uint32_t *err, uint32_t spin_limit = kSpinLimit, int drop_rel_tile = -1)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     BfSmem &sm = *reinterpret_cast<BfSmem *>(smem_raw);
@@ -86,6 +87,7 @@ bf_popc_kernel(const uint64_t *__restrict__ db, int64_t n, const uint64_t *__res
     }
 
     auto issue = [&](int64_t tile, int buf) {
+        if (tile - tile_begin == drop_rel_tile) return;   // test hook: a copy that never comes
         int64_t base = tile * TB;
         int rows = (int)(n - base < (int64_t)TB ? n - base : (int64_t)TB);
         mbar_arrive_expect_tx(&sm.bar[buf], (uint32_t)rows * 512u);
@@ -104,7 +106,7 @@ bf_popc_kernel(const uint64_t *__restrict__ db, int64_t n, const uint64_t *__res
     for (int64_t tile = tile_begin, it = 0; tile < tile_end; ++tile, ++it) {
         const int buf = (int)(it & 1);
         if (tid == 0 && tile + 1 < tile_end) issue(tile + 1, buf ^ 1);
-        const bool arrived = mbar_wait(&sm.bar[buf], (uint32_t)((it >> 1) & 1));
+        const bool arrived = mbar_wait(&sm.bar[buf], (uint32_t)((it >> 1) & 1), spin_limit);
         if (__syncthreads_or(!arrived)) {      // give up together, after our copies land
             if (tid == 0) {
                 atomicOr(err, 1u);
@@ -194,7 +196,7 @@ bf_popc_kernel(const uint64_t *__restrict__ db, int64_t n, const uint64_t *__res
 
 // One warp per query: merge the split lists, then write idx, score, (A, B).
 __global__ void bf_merge_kernel(const uint64_t *__restrict__ partial, int n_split,
-                                const uint64_t *__restrict__ db, const uint64_t *__restrict__ qs,
+                                const uint64_t *__restrict__ db, int64_t n, const uint64_t *__restrict__ qs,
                                 int64_t nq, int k, uint32_t *__restrict__ idx,
                                 float *__restrict__ score, uint16_t *__restrict__ ab)
 {
@@ -204,6 +206,7 @@ __global__ void bf_merge_kernel(const uint64_t *__restrict__ partial, int n_spli
     uint64_t slot = kEmpty;
     for (int s = 0; s < n_split; ++s) {
         uint64_t c = lane < k ? partial[((int64_t)s * nq + q) * k + lane] : kEmpty;
+        if (c != kEmpty && (int64_t)(uint32_t)c >= n) c = kEmpty;   // never index past the database
         warp_list_merge(slot, c, k, lane);
     }
     // |q| with the warp, 16 bytes a lane
@@ -264,13 +267,13 @@ int pick_bf_splits(int64_t row_blocks, int64_t tiles, int concurrent)
     return pick_splits(row_blocks, tiles, concurrent);
 }
 
-int launch_merge_partials(const uint64_t *partial, int n_split, const uint64_t *db,
+int launch_merge_partials(const uint64_t *partial, int n_split, const uint64_t *db, int64_t n,
                           const uint64_t *q, int64_t nq, int k, uint32_t *idx, float *score,
                           uint16_t *ab, cudaStream_t s)
 {
     const int wpb = 8;
-    bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(partial, n_split, db, q,
-                                                                           nq, k, idx, score, ab);
+    bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(partial, n_split, db, n,
+                                                                           q, nq, k, idx, score, ab);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
@@ -289,6 +292,11 @@ int launch_bf_popc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq,
 {
     return launch_bf_popc_cfg(db, n, q, nq, k, idx, score, ab, s, nullptr);
 }
+
+// Test hook (dt_debug_inject_missing_copy): the next popcount launches skip
+// the copy of each CTA's first tile and give up waiting for it after a few
+// thousand polls, so the timeout path runs and reports DT_ETIMEOUT.
+static std::atomic<int> g_drop_copy{0};
 
 int launch_bf_popc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                        uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s,
@@ -313,20 +321,26 @@ int launch_bf_popc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t
     const int64_t tiles_per_split = (tiles + splits - 1) / splits;
     const int n_split = (int)((tiles + tiles_per_split - 1) / tiles_per_split);
 
+    Scratch scratch(s);
     uint64_t *partial = nullptr;
     uint32_t *err = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)n_split * nq * k * sizeof(uint64_t), s));
+    DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_split * nq * k * sizeof(uint64_t)));
+    // every list starts empty, so a block that gives up leaves valid (empty) lists
+    DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_split * nq * k * sizeof(uint64_t), s));
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_bf_error));
     dim3 grid((unsigned)qblocks, (unsigned)n_split);
-    bf_popc_kernel<<<grid, THREADS, smem, s>>>(db, n, q, nq, k, tiles_per_split, partial, err);
+    const bool drop = g_drop_copy.load() != 0;
+    bf_popc_kernel<<<grid, THREADS, smem, s>>>(db, n, q, nq, k, tiles_per_split, partial, err,
+                                               drop ? 4096u : kSpinLimit, drop ? 0 : -1);
     DT_CUDA_TRY(cudaGetLastError());
     const int wpb = 8;
-    bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(partial, n_split, db, q,
-                                                                           nq, k, idx, score, ab);
+    bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(partial, n_split, db, n,
+                                                                           q, nq, k, idx, score, ab);
     DT_CUDA_TRY(cudaGetLastError());
-    DT_CUDA_TRY(cudaFreeAsync(partial, s));
     return DT_OK;
 }
+
+void set_drop_copy(bool on) { g_drop_copy.store(on ? 1 : 0); }
 
 // ---------------------------------------------------------------------------
 // Brute force without any allocation (bf_search_noalloc).
@@ -334,9 +348,9 @@ int launch_bf_popc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t
 // The only scratch the brute force needs is the per-split top-k lists that
 // the merge kernel combines.  Here they live in one fixed array compiled into
 // the library, so the call makes no cudaMalloc / cudaMallocAsync / cudaFree.
-// The array is shared by every call on a device and keeps the previous
-// call's contents; nothing in it has to start at zero, because every list
-// entry that the merge reads is written first by the same call.  Two calls
+// The array is shared by every call on a device; each call first fills the
+// lists it uses with the empty pattern (a stream-ordered memset), so a block
+// that gives up on a wait still leaves valid lists for the merge.  Two calls
 // whose work overlaps on the GPU (different streams, no ordering between
 // them) use the same array and race.
 // ---------------------------------------------------------------------------
@@ -405,11 +419,12 @@ int launch_bf_popc_noalloc(const uint64_t *db, int64_t n, const uint64_t *q, int
     const int64_t tiles_per_split = (tiles + splits - 1) / splits;
     const int n_split = (int)((tiles + tiles_per_split - 1) / tiles_per_split);
     dim3 grid((unsigned)qblocks, (unsigned)n_split);
+    DT_CUDA_TRY(cudaMemsetAsync(d->partial, 0xFF, (size_t)n_split * list_bytes, s));
     bf_popc_kernel<<<grid, THREADS, smem, s>>>(db, n, q, nq, k, tiles_per_split, d->partial, d->err);
     DT_CUDA_TRY(cudaGetLastError());
     const int wpb = 8;
-    bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(d->partial, n_split, db, q,
-                                                                           nq, k, idx, score, ab);
+    bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(d->partial, n_split, db, n,
+                                                                           q, nq, k, idx, score, ab);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }

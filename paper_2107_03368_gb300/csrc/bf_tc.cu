@@ -561,8 +561,8 @@ __global__ void merge_top1_kernel(const uint64_t *__restrict__ partial, int n_sp
 // Per-split top-k lists of every query over db (rows reported through
 // idx_map when given).  *partial is allocated on the stream; the caller frees it.
 int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
-                    int64_t nq, int k, cudaStream_t s, uint64_t **partial_out, int *n_split_out,
-                    const TuneCfg *cfg)
+                    int64_t nq, int k, cudaStream_t s, Scratch &scratch, uint64_t **partial_out,
+                    int *n_split_out, const TuneCfg *cfg)
 {
     static std::once_flag attr_once;
     static cudaError_t attr_err = cudaSuccess;
@@ -589,9 +589,11 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     uint32_t *qpop = nullptr, *err = nullptr;
     uint64_t *partial = nullptr;
     const size_t a_bytes = (size_t)n_mtiles * NCHUNK * A_STAGE;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&a_exp, a_bytes, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&qpop, (size_t)nq * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)n_split * nq * k * 8, s));
+    DT_CUDA_TRY(scratch.alloc(&a_exp, a_bytes));
+    DT_CUDA_TRY(scratch.alloc(&qpop, (size_t)nq * 4));
+    DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_split * nq * k * 8));
+    // lists start empty: a block that gives up on a wait leaves valid lists
+    DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_split * nq * k * 8, s));
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
     const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
     widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, nq, n_mtiles, a_exp, qpop);
@@ -615,8 +617,6 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.err = err;
     bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
-    cudaFreeAsync(qpop, s);
-    cudaFreeAsync(a_exp, s);
     *partial_out = partial;
     *n_split_out = n_split;
     return DT_OK;
@@ -648,8 +648,9 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     if (max_tiles <= 0) return DT_OK;
     unsigned char *a_exp = nullptr;
     uint32_t *qpop = nullptr, *err = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&a_exp, (size_t)max_tiles * NCHUNK * A_STAGE, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&qpop, (size_t)max_tiles * TM * 4, s));
+    Scratch scratch(s);
+    DT_CUDA_TRY(scratch.alloc(&a_exp, (size_t)max_tiles * NCHUNK * A_STAGE));
+    DT_CUDA_TRY(scratch.alloc(&qpop, (size_t)max_tiles * TM * 4));
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
     const int64_t items = max_tiles * TM * NCHUNK;
     widen_gather_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, slot_q, n_tiles,
@@ -670,42 +671,36 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     const int grid = (int)std::min<int64_t>(max_tiles, sm_count());   // units <= tiles
     bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
-    DT_CUDA_TRY(cudaFreeAsync(qpop, s));
-    DT_CUDA_TRY(cudaFreeAsync(a_exp, s));
     return DT_OK;
 }
 
 int launch_bf_tc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                      uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s, const TuneCfg *cfg)
 {
+    Scratch scratch(s);
     uint64_t *partial = nullptr;
     int n_split = 0;
-    if (int r = tc_partial_topk(db, n, nullptr, q, nq, k, s, &partial, &n_split, cfg)) return r;
-    int rc = launch_merge_partials(partial, n_split, db, q, nq, k, idx, score, ab, s);
-    cudaFreeAsync(partial, s);
-    return rc;
+    if (int r = tc_partial_topk(db, n, nullptr, q, nq, k, s, scratch, &partial, &n_split, cfg))
+        return r;
+    return launch_merge_partials(partial, n_split, db, n, q, nq, k, idx, score, ab, s);
 }
 
 int launch_bf_tc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                  uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s)
 {
-    uint64_t *partial = nullptr;
-    int n_split = 0;
-    if (int r = tc_partial_topk(db, n, nullptr, q, nq, k, s, &partial, &n_split, nullptr)) return r;
-    int rc = launch_merge_partials(partial, n_split, db, q, nq, k, idx, score, ab, s);
-    cudaFreeAsync(partial, s);
-    return rc;
+    return launch_bf_tc_cfg(db, n, q, nq, k, idx, score, ab, s, nullptr);
 }
 
 int launch_tc_top1(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
                    int64_t nq, uint32_t *nn, cudaStream_t s)
 {
+    Scratch scratch(s);
     uint64_t *partial = nullptr;
     int n_split = 0;
-    if (int r = tc_partial_topk(db, n, idx_map, q, nq, 1, s, &partial, &n_split, nullptr)) return r;
+    if (int r = tc_partial_topk(db, n, idx_map, q, nq, 1, s, scratch, &partial, &n_split, nullptr))
+        return r;
     merge_top1_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(partial, n_split, nq, nn);
     DT_CUDA_TRY(cudaGetLastError());
-    cudaFreeAsync(partial, s);
     return DT_OK;
 }
 

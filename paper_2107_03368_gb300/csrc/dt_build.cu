@@ -422,7 +422,7 @@ struct Grow {
         if (need <= bytes) return DT_OK;
         size_t nb = std::max(need, bytes * 2);
         void *q = nullptr;
-        DT_CUDA_TRY(cudaMallocAsync(&q, nb, s));
+        DT_CUDA_TRY(dt_malloc_async(&q, nb, s));
         if (p) {
             DT_CUDA_TRY(cudaMemcpyAsync(q, p, bytes, cudaMemcpyDeviceToDevice, s));
             DT_CUDA_TRY(cudaFreeAsync(p, s));
@@ -503,9 +503,9 @@ int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fu
     } while (0)
 
     {
-        BUILD_CUDA(cudaMallocAsync((void **)&perm, (size_t)n * 4, s));
-        BUILD_CUDA(cudaMallocAsync((void **)&tmp, (size_t)n * 4, s));
-        BUILD_CUDA(cudaMallocAsync((void **)&mk, (size_t)n * 8, s));
+        BUILD_CUDA(dt_malloc_async((void **)&perm, (size_t)n * 4, s));
+        BUILD_CUDA(dt_malloc_async((void **)&tmp, (size_t)n * 4, s));
+        BUILD_CUDA(dt_malloc_async((void **)&mk, (size_t)n * 8, s));
         iota_kernel<<<std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(perm, n);
         BUILD_CUDA(cudaGetLastError());
 

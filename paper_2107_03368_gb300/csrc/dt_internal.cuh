@@ -126,6 +126,42 @@ void set_error(const std::string &msg);
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Every scratch allocation of the library: cudaMallocAsync, except that a
+// test hook (dt_debug_fail_allocation) can make the n-th one report
+// cudaErrorMemoryAllocation.
+cudaError_t dt_malloc_async(void **p, size_t bytes, cudaStream_t s);
+
+// Stream-ordered scratch of one call: every buffer it hands out is freed on
+// the stream (after the work enqueued so far) when it goes out of scope, on
+// success and on every early error return alike.
+class Scratch {
+  public:
+    explicit Scratch(cudaStream_t s) : s_(s) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    ~Scratch()
+    {
+        for (int i = n_ - 1; i >= 0; --i) cudaFreeAsync(p_[i], s_);
+    }
+    template <class T> cudaError_t alloc(T **out, size_t bytes)
+    {
+        *out = nullptr;
+        if (n_ == kMax) return cudaErrorMemoryAllocation;
+        void *p = nullptr;
+        const cudaError_t e = dt_malloc_async(&p, bytes, s_);
+        if (e != cudaSuccess) return e;
+        p_[n_++] = p;
+        *out = static_cast<T *>(p);
+        return cudaSuccess;
+    }
+
+  private:
+    static constexpr int kMax = 16;
+    cudaStream_t s_;
+    void *p_[kMax] = {};
+    int n_ = 0;
+};
+
 int sm_count();
 
 // ---------------------------------------------------------------------------
@@ -182,13 +218,14 @@ int launch_bf_tc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t n
                      const TuneCfg *cfg);
 int pick_bf_splits(int64_t row_blocks, int64_t tiles, int concurrent);
 // Merge per-split sorted top-k lists partial[split][q][k] into idx/score/(A,B).
-int launch_merge_partials(const uint64_t *partial, int n_split, const uint64_t *db,
+int launch_merge_partials(const uint64_t *partial, int n_split, const uint64_t *db, int64_t n,
                           const uint64_t *q, int64_t nq, int k, uint32_t *idx, float *score,
                           uint16_t *ab, cudaStream_t s);
 int launch_bf_tc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                  uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s);
 int take_tc_error(bool *raised);
 int take_bf_error(bool *raised);   // read and clear the brute-force timeout flag
+void set_drop_copy(bool on);       // test hook of the popcount kernel (missing tile copy)
 int launch_bf_popc_noalloc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,
                            uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s);
 int launch_bf_popc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq, int k,

@@ -150,10 +150,11 @@ int launch_dt_search_cfg(const dt_index *ix, const uint64_t *q, int64_t nq, int 
     const int stack_cap = ix->depth + 2;
     const int64_t nwarps = blocks * (nt / 32);
 
+    Scratch scratch(s);
     SearchCtl *ctl = nullptr;
     uint64_t *stacks = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&ctl, sizeof(SearchCtl), s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&stacks, (size_t)nwarps * stack_cap * 8, s));
+    DT_CUDA_TRY(scratch.alloc(&ctl, sizeof(SearchCtl)));
+    DT_CUDA_TRY(scratch.alloc(&stacks, (size_t)nwarps * stack_cap * 8));
     DT_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(SearchCtl), s));
     kern<<<(unsigned)blocks, nt, 0, s>>>(tv, ix->iperm, q, nq, k, seeds, n_seed, ix->n, stacks,
                                          stack_cap, ctl, idx, score, ab);
@@ -172,8 +173,6 @@ int launch_dt_search_cfg(const dt_index *ix, const uint64_t *q, int64_t nq, int 
             rc = DT_ECUDA;
         }
     }
-    DT_CUDA_TRY(cudaFreeAsync(stacks, s));
-    DT_CUDA_TRY(cudaFreeAsync(ctl, s));
     return rc;
 }
 

@@ -453,13 +453,14 @@ int launch_embed_tc(const float *P, const uint64_t *bits, int64_t n, __nv_bfloat
 {
     if (n <= 0) return DT_OK;
     const int64_t nb = std::min<int64_t>(n, BATCH);
+    Scratch scratch(s);
     unsigned char *wimg = nullptr;
     __nv_bfloat16 *a1 = nullptr, *a2 = nullptr, *feat = nullptr, *h = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&wimg, (size_t)WTOT, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&a1, (size_t)nb * A1 * 2, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&a2, (size_t)nb * A2 * 2, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&feat, (size_t)nb * F0 * 2, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&h, (size_t)nb * F1 * 2, s));
+    DT_CUDA_TRY(scratch.alloc(&wimg, (size_t)WTOT));
+    DT_CUDA_TRY(scratch.alloc(&a1, (size_t)nb * A1 * 2));
+    DT_CUDA_TRY(scratch.alloc(&a2, (size_t)nb * A2 * 2));
+    DT_CUDA_TRY(scratch.alloc(&feat, (size_t)nb * F0 * 2));
+    DT_CUDA_TRY(scratch.alloc(&h, (size_t)nb * F1 * 2));
     weight_image_kernel<<<(unsigned)((WTOT / 2 + 255) / 256), 256, 0, s>>>(P, wimg);
     DT_CUDA_TRY(cudaGetLastError());
     int rc = DT_OK;
@@ -478,11 +479,6 @@ int launch_embed_tc(const float *P, const uint64_t *bits, int64_t n, __nv_bfloat
         if (rc == DT_OK) rc = launch_gemm<FC1>(g4, s);
         if (rc == DT_OK) rc = launch_gemm<FC2>(g5, s);
     }
-    cudaFreeAsync(h, s);
-    cudaFreeAsync(feat, s);
-    cudaFreeAsync(a2, s);
-    cudaFreeAsync(a1, s);
-    cudaFreeAsync(wimg, s);
     return rc;
 }
 

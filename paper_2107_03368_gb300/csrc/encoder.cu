@@ -727,15 +727,15 @@ int enc_embed(const dt_encoder *e, const uint64_t *d_bits, int64_t n, uint16_t *
                                     (int)EMBED_SMEM);
     });
     DT_CUDA_TRY(attr);
+    Scratch scratch(s);
     float *T = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&T, (size_t)TTOT * 4, s));
+    DT_CUDA_TRY(scratch.alloc(&T, (size_t)TTOT * 4));
     relayout_kernel<<<blocks_for(TTOT), 256, 0, s>>>(e->P, T);
     const int64_t groups = (n + EG - 1) / EG;
     const unsigned grid = (unsigned)std::min<int64_t>(groups, (int64_t)sm_count());   // one CTA per SM fits
     embed_kernel<<<grid, ET, EMBED_SMEM, s>>>(d_bits, n, e->P, T,
                                               reinterpret_cast<__nv_bfloat16 *>(d_out_bf16), d_out_f32);
     DT_CUDA_TRY(cudaGetLastError());
-    DT_CUDA_TRY(cudaFreeAsync(T, s));
     return DT_OK;
 }
 
@@ -777,19 +777,18 @@ int enc_train_step(dt_encoder *e, const uint64_t *d_q, const uint64_t *d_t, int3
     // conv1's input gradient is not needed; its output gradient da1 is:
     {
         // da1 = conv2^T(da2) * (a1 > 0), kept in a scratch region sized M * A1
+        Scratch scratch(s);
         float *buf = nullptr;
-        DT_CUDA_TRY(cudaMallocAsync((void **)&buf, (size_t)M * A1 * 4, s));
+        DT_CUDA_TRY(scratch.alloc(&buf, (size_t)M * A1 * 4));
         conv_bwd_data<<<blocks_for((int64_t)M * A1), 256, 0, s>>>(w.da2, P + OW2, M, C1, H1, C2, H2, w.a1, buf);
         // bits of both towers, contiguous in the order of the activations
         uint64_t *bits = nullptr;
-        DT_CUDA_TRY(cudaMallocAsync((void **)&bits, (size_t)M * kWords * 8, s));
+        DT_CUDA_TRY(scratch.alloc(&bits, (size_t)M * kWords * 8));
         DT_CUDA_TRY(cudaMemcpyAsync(bits, d_q, (size_t)B * kWords * 8, cudaMemcpyDeviceToDevice, s));
         DT_CUDA_TRY(cudaMemcpyAsync(bits + (size_t)B * kWords, d_t, (size_t)B * kWords * 8,
                                     cudaMemcpyDeviceToDevice, s));
         conv_bwd_weight<<<dim3(blocks_for((int64_t)C1 * 9 + C1), gyc), 256, 0, s>>>(
             buf, nullptr, bits, M, 1, 64, C1, H1, cc, G + OW1, G + OB1);
-        cudaFreeAsync(bits, s);
-        cudaFreeAsync(buf, s);
     }
     DT_CUDA_TRY(cudaGetLastError());
     if (update) {

@@ -501,10 +501,10 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
         set_error(std::string("ivf_build: ") + what);
         rc = DT_ECUDA;
     };
-    if (cudaMallocAsync((void **)&emb, (size_t)n * D * 2, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&assign, (size_t)n * 4, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&counts, (size_t)K * 4, s) != cudaSuccess ||
-        cudaMallocAsync((void **)&sums, (size_t)K * D * 4, s) != cudaSuccess ||
+    if (dt_malloc_async((void **)&emb, (size_t)n * D * 2, s) != cudaSuccess ||
+        dt_malloc_async((void **)&assign, (size_t)n * 4, s) != cudaSuccess ||
+        dt_malloc_async((void **)&counts, (size_t)K * 4, s) != cudaSuccess ||
+        dt_malloc_async((void **)&sums, (size_t)K * D * 4, s) != cudaSuccess ||
         cudaMalloc((void **)&ix->cent, (size_t)K * D * 4) != cudaSuccess ||
         cudaMalloc((void **)&ix->cent_t, (size_t)K * D * 4) != cudaSuccess ||
         cudaMalloc((void **)&ix->offsets, (size_t)(K + 1) * 8) != cudaSuccess ||
@@ -581,8 +581,9 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     // the list-major scan multiplies whole 128-query tiles: worth it from
     // about 10 queries per list on average (measured crossover)
     const bool tensor = path == 2 || (path == 0 && nq * n_probe >= 10LL * ix->K);
+    Scratch scratch(s);
     float *qemb = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&qemb, (size_t)nq * D * 4, s));
+    DT_CUDA_TRY(scratch.alloc(&qemb, (size_t)nq * D * 4));
     if (int r = enc_embed(enc, d_q, nq, nullptr, qemb, 0, s)) return r;
     const size_t smem = (size_t)ix->K * 4;
     if (smem > 48 * 1024)
@@ -593,7 +594,6 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
                                                          ix->offsets, ix->db, ix->ids, n_probe, k,
                                                          d_idx, d_score, nullptr, d_scanned, nullptr);
         DT_CUDA_TRY(cudaGetLastError());
-        DT_CUDA_TRY(cudaFreeAsync(qemb, s));
         return DT_OK;
     }
     // list-major: probes -> pairs grouped by list -> tensor-core units -> merge
@@ -604,18 +604,19 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     int64_t *tile_base = nullptr, *n_units = nullptr, *slot_of = nullptr;
     TcUnit *units = nullptr;
     uint64_t *partial = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&probe, (size_t)pairs * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&counts, (size_t)ix->K * 4 * 2, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&tile_base, (size_t)ix->K * 8, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&n_units, 16, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&units, (size_t)max_units * sizeof(TcUnit), s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&slot_q, (size_t)max_tiles * kTcTileM * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&slot_of, (size_t)pairs * 8, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&partial, (size_t)max_tiles * kTcTileM * k * 8, s));
+    DT_CUDA_TRY(scratch.alloc(&probe, (size_t)pairs * 4));
+    DT_CUDA_TRY(scratch.alloc(&counts, (size_t)ix->K * 4 * 2));
+    DT_CUDA_TRY(scratch.alloc(&tile_base, (size_t)ix->K * 8));
+    DT_CUDA_TRY(scratch.alloc(&n_units, 16));
+    DT_CUDA_TRY(scratch.alloc(&units, (size_t)max_units * sizeof(TcUnit)));
+    DT_CUDA_TRY(scratch.alloc(&slot_q, (size_t)max_tiles * kTcTileM * 4));
+    DT_CUDA_TRY(scratch.alloc(&slot_of, (size_t)pairs * 8));
+    DT_CUDA_TRY(scratch.alloc(&partial, (size_t)max_tiles * kTcTileM * k * 8));
     int32_t *fill = counts + ix->K;
     int64_t *n_tiles = n_units + 1;
     DT_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)ix->K * 4 * 2, s));
     DT_CUDA_TRY(cudaMemsetAsync(slot_q, 0xFF, (size_t)max_tiles * kTcTileM * 4, s));
+    DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)max_tiles * kTcTileM * k * 8, s));
     {   // probes: up to eight queries per block, as many as their scores fit in shared memory
         const size_t per_q = (size_t)ix->K * 4, room = 200 * 1024;
         const int qb = per_q * 8 <= room ? 8 : per_q * 4 <= room ? 4 : per_q * 2 <= room ? 2 : 1;
@@ -641,15 +642,6 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
                                                                    nq, k, d_idx, d_score);
         DT_CUDA_TRY(cudaGetLastError());
     }
-    cudaFreeAsync(partial, s);
-    cudaFreeAsync(slot_of, s);
-    cudaFreeAsync(slot_q, s);
-    cudaFreeAsync(units, s);
-    cudaFreeAsync(n_units, s);
-    cudaFreeAsync(tile_base, s);
-    cudaFreeAsync(counts, s);
-    cudaFreeAsync(probe, s);
-    DT_CUDA_TRY(cudaFreeAsync(qemb, s));
     return rc;
 }
 

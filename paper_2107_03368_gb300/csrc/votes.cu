@@ -288,10 +288,11 @@ int retrieve_tree(const dt_index *ix, const uint32_t *object_of, int n_objects, 
     TreeView tv{ix->node, ix->or_img, ix->and_img, ix->db_tree, ix->perm};
     const bool use_and = ix->use_and != 0;
     const int stack_cap = ix->depth + 2;
+    Scratch scratch(s);
     uint32_t *nn = nullptr, *order = nullptr;
     if (threshold > 0) {
-        DT_CUDA_TRY(cudaMallocAsync((void **)&nn, (size_t)std::max<int64_t>(total, 1) * 4, s));
-        DT_CUDA_TRY(cudaMallocAsync((void **)&order, (size_t)std::max<int64_t>(total, 1) * 4, s));
+        DT_CUDA_TRY(scratch.alloc(&nn, (size_t)std::max<int64_t>(total, 1) * 4));
+        DT_CUDA_TRY(scratch.alloc(&order, (size_t)std::max<int64_t>(total, 1) * 4));
     }
     auto k0 = use_and ? retrieve_nn_kernel<true, 0> : retrieve_nn_kernel<false, 0>;
     auto k1 = use_and ? retrieve_nn_kernel<true, 1> : retrieve_nn_kernel<false, 1>;
@@ -303,8 +304,8 @@ int retrieve_tree(const dt_index *ix, const uint32_t *object_of, int n_objects, 
     const int64_t nwarps = blocks * (VT / 32);
     VoteCtl *ctl = nullptr;
     uint64_t *stacks = nullptr;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&ctl, sizeof(VoteCtl), s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&stacks, (size_t)nwarps * stack_cap * 8, s));
+    DT_CUDA_TRY(scratch.alloc(&ctl, sizeof(VoteCtl)));
+    DT_CUDA_TRY(scratch.alloc(&stacks, (size_t)nwarps * stack_cap * 8));
     DT_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(VoteCtl), s));
     kern<<<(unsigned)blocks, VT, 0, s>>>(tv, object_of, n_objects, qdesc, qoffsets, nq, stacks,
                                          stack_cap, ctl, votes, nn);
@@ -317,10 +318,6 @@ int retrieve_tree(const dt_index *ix, const uint32_t *object_of, int n_objects, 
         winner_kernel<<<(nq + 7) / 8, 256, 0, s>>>(votes, n_objects, qoffsets, nq, winner, consumed);
     }
     DT_CUDA_TRY(cudaGetLastError());
-    DT_CUDA_TRY(cudaFreeAsync(stacks, s));
-    DT_CUDA_TRY(cudaFreeAsync(ctl, s));
-    if (nn) DT_CUDA_TRY(cudaFreeAsync(nn, s));
-    if (order) DT_CUDA_TRY(cudaFreeAsync(order, s));
     return DT_OK;
 }
 
@@ -329,9 +326,10 @@ int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects
                     int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
                     int64_t *consumed, cudaStream_t s)
 {
+    Scratch scratch(s);
     if (threshold == 0) {
         uint32_t *nn = nullptr;
-        DT_CUDA_TRY(cudaMallocAsync((void **)&nn, (size_t)std::max<int64_t>(total, 1) * 4, s));
+        DT_CUDA_TRY(scratch.alloc(&nn, (size_t)std::max<int64_t>(total, 1) * 4));
         if (total > 0) {
             if (int r = launch_tc_top1(ix->db_tree, ix->n, ix->perm, qdesc, total, nn, s)) return r;
             vote_all_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(
@@ -339,18 +337,17 @@ int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects
         }
         winner_kernel<<<(nq + 7) / 8, 256, 0, s>>>(votes, n_objects, qoffsets, nq, winner, consumed);
         DT_CUDA_TRY(cudaGetLastError());
-        DT_CUDA_TRY(cudaFreeAsync(nn, s));
         return DT_OK;
     }
     // rounds of draws
     uint32_t *order = nullptr;
     RoundState st;
-    DT_CUDA_TRY(cudaMallocAsync((void **)&order, (size_t)std::max<int64_t>(total, 1) * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&st.used, (size_t)nq * 8, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&st.done, (size_t)nq * 4, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&st.take, (size_t)nq * 8, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&st.slot, (size_t)nq * 8, s));
-    DT_CUDA_TRY(cudaMallocAsync((void **)&st.total, 8, s));
+    DT_CUDA_TRY(scratch.alloc(&order, (size_t)std::max<int64_t>(total, 1) * 4));
+    DT_CUDA_TRY(scratch.alloc(&st.used, (size_t)nq * 8));
+    DT_CUDA_TRY(scratch.alloc(&st.done, (size_t)nq * 4));
+    DT_CUDA_TRY(scratch.alloc(&st.take, (size_t)nq * 8));
+    DT_CUDA_TRY(scratch.alloc(&st.slot, (size_t)nq * 8));
+    DT_CUDA_TRY(scratch.alloc(&st.total, 8));
     DT_CUDA_TRY(cudaMemsetAsync(st.used, 0, (size_t)nq * 8, s));
     DT_CUDA_TRY(cudaMemsetAsync(st.done, 0, (size_t)nq * 4, s));
     DT_CUDA_TRY(cudaMemsetAsync(winner, 0xFF, (size_t)nq * 4, s));   // -1
@@ -371,10 +368,11 @@ int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects
             break;
         }
         if (batch_n == 0) break;
+        Scratch round(s);                      // this round's batch, freed at its end
         uint64_t *batch = nullptr;
         uint32_t *nn = nullptr;
-        if (cudaMallocAsync((void **)&batch, (size_t)batch_n * 512, s) != cudaSuccess ||
-            cudaMallocAsync((void **)&nn, (size_t)batch_n * 4, s) != cudaSuccess) {
+        if (round.alloc(&batch, (size_t)batch_n * 512) != cudaSuccess ||
+            round.alloc(&nn, (size_t)batch_n * 4) != cudaSuccess) {
             set_error("retrieve_objects: batch allocation failed");
             rc = DT_ENOMEM;
             break;
@@ -384,19 +382,11 @@ int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects
         if (rc == DT_OK)
             round_replay_kernel<<<(nq + 127) / 128, 128, 0, s>>>(nn, object_of, n_objects, qoffsets,
                                                                 nq, threshold, st, votes, winner);
-        cudaFreeAsync(nn, s);
-        cudaFreeAsync(batch, s);
         if (rc != DT_OK) break;
         C *= 2;
     }
     if (rc == DT_OK)
         round_finish_kernel<<<(nq + 127) / 128, 128, 0, s>>>(votes, n_objects, nq, st, winner, consumed);
-    cudaFreeAsync(st.total, s);
-    cudaFreeAsync(st.slot, s);
-    cudaFreeAsync(st.take, s);
-    cudaFreeAsync(st.done, s);
-    cudaFreeAsync(st.used, s);
-    cudaFreeAsync(order, s);
     DT_CUDA_TRY(cudaGetLastError());
     return rc;
 }

@@ -83,6 +83,8 @@ def load():
             "retrieve_objects": ([P, P, i32, P, P, i32, i64, i32, u64, P, P, P, i32, P],
                                  ctypes.c_int),
             "dt_sync_status": ([P], ctypes.c_int),
+            "dt_debug_fail_allocation": ([i32], None),
+            "dt_debug_inject_missing_copy": ([i32], None),
             "dt_autotune": ([P, P, i64, P, i64, i32, P, P], ctypes.c_int),
             "dt_tune_save": ([ctypes.c_char_p], ctypes.c_int),
             "dt_tune_load": ([ctypes.c_char_p], ctypes.c_int),
@@ -292,6 +294,17 @@ def dt_tune_clear():
 
 def dt_sync_status(stream=None):
     _check(load().dt_sync_status(_stream(stream)), "dt_sync_status")
+
+
+def dt_debug_fail_allocation(nth):
+    """Test hook: the nth scratch allocation from now fails (0 = off)."""
+    load().dt_debug_fail_allocation(int(nth))
+
+
+def dt_debug_inject_missing_copy(on):
+    """Test hook: popcount brute-force launches lose one tile copy and time
+    out (dt_sync_status then reports DT_ETIMEOUT) until switched off."""
+    load().dt_debug_inject_missing_copy(1 if on else 0)
 
 
 def dt_status_string(status):
