@@ -177,3 +177,33 @@ def test_ivf_list_major_tensor_path_equals_per_query_path(k, n_probe):
     assert np.all(s[:, -1] >= o_score[:, -1] * (1 - 1e-6))
     assert np.all(np.diff(s, axis=1) >= 0)
     del got
+
+
+def test_ivf_edges_on_both_paths():
+    """One query; k larger than the rows of the probed lists (short results
+    padded with 0xFFFFFFFF / inf); lists that no descriptor fell into."""
+    enc = learned.Encoder(seed=21)
+    db = mixed_db(9, 300, per_object=30)
+    d_db = to_dev(db)
+    ivf = learned.IVF(enc, d_db, n_lists=64, iters=2)
+    off = ivf.offsets()
+    sizes = np.diff(off)
+    q, _ = synth.queries(10, db, 5)
+    d_q = to_dev(q)
+    for path in (1, 2):
+        # a single query, every list probed: the exact top-k
+        idx, score, scanned = ivf.search(d_q[:1], 7, n_probe=64, with_scanned=True, path=path)
+        o_idx, o_score, _ = oracle.bf_topk(db, q[:1], 7)
+        assert np.array_equal(idx_np(idx), o_idx)
+        np.testing.assert_allclose(score.cpu().numpy(), o_score, rtol=1e-6)
+        assert scanned.item() == db.shape[0]
+        # one probe, k far above any list's size: valid rows first, then padding
+        idx1, score1, sc1 = ivf.search(d_q, 32, n_probe=1, with_scanned=True, path=path)
+        got = idx_np(idx1)
+        s1 = score1.cpu().numpy()
+        for r in range(q.shape[0]):
+            m = int(sc1[r].item())
+            assert m <= sizes.max()
+            assert np.all(got[r, :m] < db.shape[0]) and np.all(np.isfinite(s1[r, :m]))
+            assert np.all(got[r, m:] == 0xFFFFFFFF) and np.all(np.isinf(s1[r, m:]))
+            assert np.all(np.diff(s1[r, :m]) >= 0)
