@@ -376,6 +376,7 @@ def run_ours(a, dist):
     for name, path in (("popc", 1), ("tensor", 2)):
         ms_bf, same = time_bf(dt, d_db, d_q, k, path, a.bf_steps, stream, tree_idx)
         bf[name] = {"queries_per_s": a.nq / (ms_bf / 1000.0), "ms": ms_bf,
+                    "descriptors_scanned_per_s": a.nq * a.n / (ms_bf / 1000.0),
                     "same_indices_as_tree": same}
     bf_best = max(v["queries_per_s"] for v in bf.values())
     # their own rooflines: the popcount kernel is bound by the POPC pipe
@@ -413,6 +414,7 @@ def run_ours(a, dist):
         "build_s": build_s,
         "graph_replay": graph,
         "gpu_traversal_per_query": {kk: v / a.nq for kk, v in gst.items()},
+        "descriptors_scanned_per_s": gst["descs_scanned"] / (ms / 1000.0) * dist.world,
     }
 
     if not a.no_votes:
@@ -602,7 +604,8 @@ def learned_leg(a, dist, d_db, d_q, db, tree_qps, bf_qps, stream, ix, tree_idx):
         tf = 2.0 * 4096 * scanned * a.nq / (ms / 1e3) / 1e12
         tc_peak = 2.0 * peaks()["bf16_tflops"]
         out.update(n_probe=chosen, recall_at_1=rec, queries_per_s=qps, ms=ms,
-                   scanned_per_query=scanned, speedup_vs_tree=qps / tree_qps,
+                   scanned_per_query=scanned, descriptors_scanned_per_s=qps * scanned,
+                   speedup_vs_tree=qps / tree_qps,
                    speedup_vs_bf=qps / bf_qps,
                    scan_roofline={"bound": "tensor", "achieved": tf, "peak": tc_peak,
                                   "unit": "TFLOP/s", "frac": tf / tc_peak,
