@@ -12,6 +12,7 @@ Functions and the passages they follow:
   node_bound                     node lower bound (§4.2)
   tree_search                    best-first Dissimilarity Tree query (§4.2)
   permutation / retrieve         voting pipeline (§3)
+  object_scores                  object distance score (§6.4)
 
 Every function is pinned by tests under ``tests/`` against closed forms,
 invariants and brute force (see ``tests/test_oracle_*.py``).
@@ -72,6 +73,8 @@ def _load():
         lib.orc_permutation.argtypes = [u64, i64, i64, P]
         lib.orc_permutation.restype = None
         lib.orc_retrieve.argtypes = [P, i64, P, i32, P, P, i32, i32, u64, P, P, P, i32]
+        lib.orc_object_scores.argtypes = [P, i64, P, i32, P, P, i32, P, i32]
+        lib.orc_object_scores.restype = None
         lib.orc_retrieve.restype = None
         _lib = lib
     return _lib
@@ -232,3 +235,17 @@ def retrieve(db, object_of, n_objects, qdesc, offsets, threshold, seed, nthreads
                          nq, threshold, ctypes.c_uint64(seed), _p(votes), _p(winner),
                          _p(consumed), _threads(nthreads))
     return votes[:nq], winner[:nq], consumed[:nq]
+
+
+def object_scores(db, object_of, n_objects, qdesc, offsets, nthreads=0):
+    """scores float64 [nq][n_objects]: for each query object, the sum over its
+    descriptors of the Eq. 1 distance to the nearest descriptor of each
+    database object (+inf for an object without descriptors)."""
+    db, qdesc = _desc(db), _desc(qdesc)
+    obj = np.ascontiguousarray(object_of, dtype=np.uint32)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    nq = off.shape[0] - 1
+    out = np.empty((nq, n_objects), dtype=np.float64)
+    _load().orc_object_scores(_p(db), db.shape[0], _p(obj), n_objects, _p(qdesc), _p(off), nq,
+                              _p(out), _threads(nthreads))
+    return out

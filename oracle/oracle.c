@@ -652,3 +652,40 @@ void orc_retrieve(const uint64_t *db, int64_t n, const uint32_t *object_of, int3
         free(order);
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Object distance score (§6.4)                                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The distance score of a (query object, complete object) pair is the sum,
+ * over the descriptors of the query object, of each one's Eq. 1 distance to
+ * its nearest descriptor of the complete object.  scores[j][o] for query j
+ * (descriptors offsets[j] .. offsets[j+1]-1 of qdesc) and database object o
+ * (the descriptors t with object_of[t] == o): +inf when object o has no
+ * descriptor, 0 for a query without descriptors.  Distances in FP64 (Eq. 1
+ * as A/P + B/Z); the minimum per object, then the plain sum.
+ */
+void orc_object_scores(const uint64_t *db, int64_t n, const uint32_t *object_of, int32_t n_objects,
+                       const uint64_t *qdesc, const int64_t *offsets, int32_t nq, double *scores,
+                       int32_t nthreads)
+{
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int32_t j = 0; j < nq; ++j) {
+        double *row = scores + (int64_t)j * n_objects;
+        double *best = (double *)malloc(sizeof(double) * (size_t)(n_objects > 0 ? n_objects : 1));
+        for (int32_t o = 0; o < n_objects; ++o) row[o] = 0.0;
+        for (int64_t i = offsets[j]; i < offsets[j + 1]; ++i) {
+            const uint64_t *q = qdesc + i * OW;
+            for (int32_t o = 0; o < n_objects; ++o) best[o] = INFINITY;
+            for (int64_t t = 0; t < n; ++t) {
+                const uint32_t o = object_of[t];
+                if (o >= (uint32_t)n_objects) continue;
+                const double d = orc_wh(q, db + t * OW, NULL, NULL);
+                if (d < best[o]) best[o] = d;
+            }
+            for (int32_t o = 0; o < n_objects; ++o) row[o] += best[o];
+        }
+        free(best);
+    }
+}
