@@ -670,6 +670,21 @@ def votes_leg(a, dev, stream, nt):
     q_sub = d_qd[:n_desc]
     ref_votes, _, _ = dt.retrieve_objects(ix, d_obj, n_obj, q_sub, sub_off, 0, seed, engine=2)
     torch.cuda.synchronize()
+    # object distance scores (§6.4) of the same sample against every object
+    torch.cuda.synchronize()
+    s_ev = torch.cuda.Event(enable_timing=True)
+    e_ev = torch.cuda.Event(enable_timing=True)
+    s_ev.record(stream)
+    with nvtx("object_scores"):
+        sc = dt.object_scores(d_db, d_obj, n_obj, q_sub, sub_off)
+    e_ev.record(stream)
+    torch.cuda.synchronize()
+    ms_s = s_ev.elapsed_time(e_ev)
+    best = sc.argmin(dim=1).cpu().numpy()
+    out["object_scores_sample"] = {
+        "partial_queries": m, "query_descriptors": n_desc, "objects": n_obj, "ms": ms_s,
+        "pairs_per_s": n_desc * (n_obj * per) / (ms_s / 1e3),
+        "best_object_is_source": float(np.mean(best == qobj[:m]))}
     out["threshold_0_sample"]["graph_replay"] = graph_replay_leg(
         lambda: dt.retrieve_objects(ix, d_obj, n_obj, q_sub, sub_off, 0, seed, engine=2, out=vo),
         vo[0], ref_votes, stream)

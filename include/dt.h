@@ -257,6 +257,27 @@ int retrieve_objects(const dt_index *index, const uint32_t *d_object_of_desc, in
 int dt_sync_status(void *stream);
 
 /*
+ * object_scores — object distance scores (§6.4): scores[j][o] = sum over
+ * the descriptors of query object j of each one's Eq. 1 distance to its
+ * nearest descriptor of database object o (the descriptors t with
+ * object_of[t] == o).  +inf where object o has no descriptor (and query j
+ * has some); 0 for a query object without descriptors.
+ *
+ * d_db [n][64], d_object_of [n] uint32 (ids >= n_objects are ignored),
+ * d_qdesc [n_qdesc][64] with query j = rows d_qoffsets[j] .. d_qoffsets[j+1]-1
+ * (device int64 [nq+1], from 0 to n_qdesc, non-decreasing), d_scores
+ * [nq][n_objects] FP64.  Every pair is compared (tensor cores, exact
+ * integer keys); each per-object minimum becomes key / (P Z) in FP64 and
+ * the sums are taken in FP64.  Reads the offsets to the host and
+ * synchronises the stream.  Scratch: a copy of the database grouped by
+ * object (n * 512 bytes) plus about 1 GiB.
+ * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA.
+ */
+int object_scores(const uint64_t *d_db, int64_t n, const uint32_t *d_object_of, int32_t n_objects,
+                  const uint64_t *d_qdesc, const int64_t *d_qoffsets, int32_t nq, int64_t n_qdesc,
+                  double *d_scores, void *stream);
+
+/*
  * dt_autotune — pick launch shapes by timing them on the caller's data.
  * The paper has no counterpart; results never depend on the shapes, only
  * speed.  With `index`, the tree traversal's threads per block and resident

@@ -31,6 +31,7 @@ CUDA_SOURCES = [
     "encoder.cu",
     "enc_tc.cu",
     "ivf.cu",
+    "objects.cu",
     "votes.cu",
 ]
 

@@ -236,7 +236,7 @@ struct TcArgs {
 // >= nvalid[i] of tile i are padding.
 struct Unit {
     int64_t mt[QT];
-    int64_t r0, r1, ntiles, sp;
+    int64_t r0, r1, ntiles, sp, out_base;
     int nvalid[QT];
 };
 
@@ -251,11 +251,13 @@ __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
         v.r1 = t.row1;
         v.ntiles = (t.row1 - t.row0 + TN - 1) / TN;
         v.sp = 0;
+        v.out_base = t.out_base;
         v.nvalid[0] = t.nvalid0;
         v.nvalid[1] = t.a_tile1 >= 0 ? t.nvalid1 : 0;
     } else {
         const int64_t mp = u % a.n_mpairs;
         v.sp = u / a.n_mpairs;
+        v.out_base = 0;
         const int64_t t0 = v.sp * a.tiles_per_split;
         const int64_t t1 = min(a.n_ntiles, t0 + a.tiles_per_split);
         v.r0 = t0 * TN;
@@ -527,7 +529,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
             }
             if (valid) {
-                uint64_t *out = args.units ? args.partial + qi * k
+                uint64_t *out = args.units ? args.partial + (uv.out_base + qi) * k
                                            : args.partial + (uv.sp * nq + qi) * k;
                 for (int j = 0; j < k; ++j) out[j] = L[j];
             }
@@ -669,6 +671,52 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.partial = partial;
     a.err = err;
     const int grid = (int)std::min<int64_t>(max_tiles, sm_count());   // units <= tiles
+    bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
+    DT_CUDA_TRY(cudaGetLastError());
+    return DT_OK;
+}
+
+size_t tc_tile_bytes() { return (size_t)NCHUNK * A_STAGE; }
+
+int launch_widen_queries(const uint64_t *q, int64_t nq, unsigned char *a_exp, uint32_t *qpop,
+                         cudaStream_t s)
+{
+    if (nq <= 0) return DT_OK;
+    const int n_mtiles = (int)((nq + TM - 1) / TM);
+    const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
+    widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, nq, n_mtiles, a_exp, qpop);
+    DT_CUDA_TRY(cudaGetLastError());
+    return DT_OK;
+}
+
+int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
+                        const unsigned char *a_exp, const uint32_t *qpop, const TcUnit *units,
+                        const int64_t *n_units, int64_t max_units, int k, uint64_t *partial,
+                        cudaStream_t s)
+{
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SMEM_BYTES);
+    });
+    DT_CUDA_TRY(attr_err);
+    if (max_units <= 0) return DT_OK;
+    uint32_t *err = nullptr;
+    DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
+    TcArgs a{};
+    a.db = db;
+    a.n = n;
+    a.a_exp = a_exp;
+    a.qpop = qpop;
+    a.idx_map = idx_map;
+    a.nq = 0;
+    a.k = k;
+    a.units = units;
+    a.n_units = n_units;
+    a.partial = partial;
+    a.err = err;
+    const int grid = (int)std::min<int64_t>(max_units, sm_count());
     bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;

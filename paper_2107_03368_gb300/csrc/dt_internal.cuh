@@ -245,6 +245,7 @@ int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects
 struct TcUnit {
     int64_t row0, row1;
     int32_t a_tile0, a_tile1, nvalid0, nvalid1;
+    int64_t out_base;    // added to the slot: results go to partial[out_base + slot][k]
 };
 // Tensor-core scan over a unit table built on the device: *n_units units
 // covering *n_tiles query tiles (at most max_tiles); the row r of tile t is
@@ -255,6 +256,17 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
                     const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
                     cudaStream_t s);
 constexpr int kTcTileM = 128;
+// Queries -> pre-widened tensor-core tiles a_exp [ceil(nq/128)][32 chunks][16 KB]
+// and |q| (qpop [ceil(nq/128) * 128]); both device buffers of the caller.
+int launch_widen_queries(const uint64_t *q, int64_t nq, unsigned char *a_exp, uint32_t *qpop,
+                         cudaStream_t s);
+size_t tc_tile_bytes();      // bytes of one pre-widened 128-query tile
+// Tensor-core scan over a unit table whose query tiles are already widened
+// (a_exp, qpop as above); *n_units units, at most max_units.
+int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
+                        const unsigned char *a_exp, const uint32_t *qpop, const TcUnit *units,
+                        const int64_t *n_units, int64_t max_units, int k, uint64_t *partial,
+                        cudaStream_t s);
 // Exact top-1 of each query over db on the tensor cores; reported indices go
 // through idx_map when given (ties are broken on the reported index).
 int launch_tc_top1(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,

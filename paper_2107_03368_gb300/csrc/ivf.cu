@@ -396,6 +396,7 @@ __global__ void unit_plan_kernel(const int32_t *__restrict__ counts, int K,
                 const bool two = 2 * i + 1 < nt;
                 u.a_tile1 = two ? (int32_t)(t0 + 2 * i + 1) : -1;
                 u.nvalid1 = two ? (int32_t)min(cnt - (2 * i + 1) * kTcTileM, (uint32_t)kTcTileM) : 0;
+                u.out_base = 0;
                 units[u0 + i] = u;
             }
         }

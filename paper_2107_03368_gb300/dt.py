@@ -83,6 +83,7 @@ def load():
             "retrieve_objects": ([P, P, i32, P, P, i32, i64, i32, u64, P, P, P, i32, P],
                                  ctypes.c_int),
             "dt_sync_status": ([P], ctypes.c_int),
+            "object_scores": ([P, i64, P, i32, P, P, i32, i64, P, P], ctypes.c_int),
             "dt_debug_fail_allocation": ([i32], None),
             "dt_debug_inject_missing_copy": ([i32], None),
             "dt_autotune": ([P, P, i64, P, i64, i32, P, P], ctypes.c_int),
@@ -294,6 +295,22 @@ def dt_tune_clear():
 
 def dt_sync_status(stream=None):
     _check(load().dt_sync_status(_stream(stream)), "dt_sync_status")
+
+
+def object_scores(db, object_of, n_objects, qdesc, qoffsets, stream=None):
+    """float64 [nq, n_objects]: per query object and database object, the sum
+    of its descriptors' distances to their nearest descriptor of the object."""
+    db, qdesc = _desc(db, "db"), _desc(qdesc, "qdesc")
+    if not (object_of.is_cuda and object_of.dtype == torch.int32 and object_of.is_contiguous()):
+        raise ValueError("object_of must be a contiguous CUDA int32 tensor")
+    if not (qoffsets.is_cuda and qoffsets.dtype == torch.int64 and qoffsets.is_contiguous()):
+        raise ValueError("qoffsets must be a contiguous CUDA int64 tensor")
+    nq = qoffsets.shape[0] - 1
+    out = torch.empty((nq, n_objects), dtype=torch.float64, device=db.device)
+    _check(load().object_scores(_ptr(db), db.shape[0], _ptr(object_of), n_objects, _ptr(qdesc),
+                                _ptr(qoffsets), nq, qdesc.shape[0], _ptr(out), _stream(stream)),
+           "object_scores")
+    return out
 
 
 def dt_debug_fail_allocation(nth):

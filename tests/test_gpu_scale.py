@@ -131,3 +131,19 @@ def test_partial_retrieval_on_full_database():
     expect = np.bincount(obj[o_nn[:, 0]], minlength=n_obj)
     assert np.array_equal(v10[j], expect)
     ix.free()
+
+
+def test_object_scores_on_full_database():
+    """Object distance scores of a few query objects against the 400 x
+    25,000 database, each checked against the oracle."""
+    n_obj, per = 400, 25_000
+    db, obj = synth.database(SEED + 2, n_obj * per, per_object=per)
+    qd, off, qobj = synth.partial_queries(SEED + 2, db, n_obj, per, 3)
+    pick = [np.arange(off[j], off[j] + 4) for j in range(3)]       # 4 descriptors of each
+    sub = np.concatenate([qd[p] for p in pick])
+    soff = np.array([0, 4, 8, 12], dtype=np.int64)
+    got = dt.object_scores(to_dev(db), torch.from_numpy(obj.view(np.int32)).cuda(), n_obj,
+                           to_dev(sub), torch.from_numpy(soff).cuda()).cpu().numpy()
+    exp = oracle.object_scores(db, obj, n_obj, sub, soff)
+    np.testing.assert_allclose(got, exp, rtol=1e-12, atol=0)
+    assert np.all(np.argmin(got, axis=1) == qobj[:3])    # the source object scores lowest
