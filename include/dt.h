@@ -180,7 +180,8 @@ int dt_search_seeded(const dt_index *index, const uint64_t *d_q, int64_t nq, int
  * accumulation in tensor memory), 0 = automatic (2 for 64 or more queries).
  * Both paths give identical results.  Allocates scratch from the
  * stream-ordered allocator.
- * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA.
+ * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA; a device wait that gave up is
+ * reported by the next dt_sync_status (DT_ETIMEOUT).
  */
 int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,
               uint32_t *d_idx, float *d_score, uint16_t *d_ab, int32_t path, void *stream);
@@ -204,10 +205,10 @@ int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, 
  *   Set-up: the first call on a device (with that device current) looks up
  *   the array's device address; make that first call before any stream
  *   capture.
- *   Sharing: all calls on a device share the array and it keeps the last
- *   call's contents (nothing in it needs to start at zero).  Calls whose
- *   work overlaps on the GPU (e.g. on two unordered streams) race on it;
- *   order them on one stream.
+ *   Sharing: all calls on a device share the array; each call first fills
+ *   the part it uses with the empty pattern (a stream-ordered memset, no
+ *   allocation).  Calls whose work overlaps on the GPU (e.g. on two
+ *   unordered streams) race on it; order them on one stream.
  * Results are identical to bf_search's.  Errors: DT_EINVAL, DT_ECUDA.
  */
 #define DT_NOALLOC_SCRATCH_BYTES (16u << 20)
