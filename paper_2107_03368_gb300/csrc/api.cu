@@ -38,6 +38,21 @@ int sm_count()
     return cached[dev];
 }
 
+cudaError_t allow_smem(const void *func, int bytes)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<const void *, int>, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &d : done)
+        if (d.first.first == func && d.first.second == dev && d.second >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.push_back({{func, dev}, bytes});
+    return e;
+}
+
 // Test hook: when positive, the n-th scratch allocation from now fails.
 static std::atomic<int> g_fail_alloc{0};
 

@@ -303,12 +303,8 @@ int launch_bf_popc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t
                        const TuneCfg *cfg)
 {
     const size_t smem = sizeof(BfSmem) + (size_t)QB * k * sizeof(uint64_t);
-    static bool attr_set = false;
-    if (!attr_set) {
-        DT_CUDA_TRY(cudaFuncSetAttribute(bf_popc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(BfSmem) + QB * kMaxK * sizeof(uint64_t))));
-        attr_set = true;
-    }
+    DT_CUDA_TRY(allow_smem((const void *)bf_popc_kernel,
+                           (int)(sizeof(BfSmem) + QB * kMaxK * sizeof(uint64_t))));
     const int64_t qblocks = (nq + QB - 1) / QB;
     const int64_t tiles = (n + TB - 1) / TB;
     int per_sm = 0;
@@ -384,8 +380,8 @@ int noalloc_setup(NoallocDevice **out)
         void *p = nullptr, *e = nullptr;
         DT_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_partial));
         DT_CUDA_TRY(cudaGetSymbolAddress(&e, g_bf_error));
-        DT_CUDA_TRY(cudaFuncSetAttribute(bf_popc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(BfSmem) + QB * kMaxK * sizeof(uint64_t))));
+        DT_CUDA_TRY(allow_smem((const void *)bf_popc_kernel,
+                               (int)(sizeof(BfSmem) + QB * kMaxK * sizeof(uint64_t))));
         d.partial = static_cast<uint64_t *>(p);
         d.err = static_cast<uint32_t *>(e);
         d.ready = true;

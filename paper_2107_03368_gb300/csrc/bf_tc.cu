@@ -566,13 +566,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
                     int64_t nq, int k, cudaStream_t s, Scratch &scratch, uint64_t **partial_out,
                     int *n_split_out, const TuneCfg *cfg)
 {
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)SMEM_BYTES);
-    });
-    DT_CUDA_TRY(attr_err);
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel, (int)SMEM_BYTES));
     const int n_mtiles = (int)((nq + TM - 1) / TM);
     const int n_mpairs = (n_mtiles + QT - 1) / QT;
     const int64_t n_ntiles = (n + TN - 1) / TN;
@@ -640,13 +634,7 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
                     const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
                     cudaStream_t s)
 {
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)SMEM_BYTES);
-    });
-    DT_CUDA_TRY(attr_err);
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel, (int)SMEM_BYTES));
     if (max_tiles <= 0) return DT_OK;
     unsigned char *a_exp = nullptr;
     uint32_t *qpop = nullptr, *err = nullptr;
@@ -694,13 +682,7 @@ int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
                         const int64_t *n_units, int64_t max_units, int k, uint64_t *partial,
                         cudaStream_t s)
 {
-    static std::once_flag attr_once;
-    static cudaError_t attr_err = cudaSuccess;
-    std::call_once(attr_once, [] {
-        attr_err = cudaFuncSetAttribute(bf_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)SMEM_BYTES);
-    });
-    DT_CUDA_TRY(attr_err);
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel, (int)SMEM_BYTES));
     if (max_units <= 0) return DT_OK;
     uint32_t *err = nullptr;
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));

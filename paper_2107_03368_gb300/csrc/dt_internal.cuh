@@ -164,6 +164,10 @@ class Scratch {
 
 int sm_count();
 
+// Let `func` use `bytes` of dynamic shared memory on the current device (a
+// per-device setting, applied once per kernel and device).
+cudaError_t allow_smem(const void *func, int bytes);
+
 // ---------------------------------------------------------------------------
 // Index
 // ---------------------------------------------------------------------------

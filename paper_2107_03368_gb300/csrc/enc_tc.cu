@@ -420,14 +420,7 @@ __global__ void weight_image_kernel(const float *__restrict__ P, unsigned char *
 template <int MODE>
 int launch_gemm(const GemmArgs &a, cudaStream_t s)
 {
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(enc_gemm_kernel<MODE>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)gemm_smem<MODE>());
-    });
-    DT_CUDA_TRY(attr);
+    DT_CUDA_TRY(allow_smem((const void *)enc_gemm_kernel<MODE>, (int)gemm_smem<MODE>()));
     const int64_t tiles = (a.rows + TM - 1) / TM;
     const int grid = (int)std::min<int64_t>(tiles, sm_count());
     enc_gemm_kernel<MODE><<<grid, THREADS, gemm_smem<MODE>(), s>>>(a);

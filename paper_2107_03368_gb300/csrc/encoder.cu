@@ -720,13 +720,7 @@ int enc_embed(const dt_encoder *e, const uint64_t *d_bits, int64_t n, uint16_t *
     if (path == 2 || (path == 0 && n >= 4096))
         return launch_embed_tc(e->P, d_bits, n, reinterpret_cast<__nv_bfloat16 *>(d_out_bf16),
                                d_out_f32, s);
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(embed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)EMBED_SMEM);
-    });
-    DT_CUDA_TRY(attr);
+    DT_CUDA_TRY(allow_smem((const void *)embed_kernel, (int)EMBED_SMEM));
     Scratch scratch(s);
     float *T = nullptr;
     DT_CUDA_TRY(scratch.alloc(&T, (size_t)TTOT * 4));
