@@ -9,6 +9,7 @@ Functions and the passages they follow:
   wh_bytes / wh_bitwise / wh     Eq. 1 (§2.3) weighted Hamming distance
   bf_topk                        sequential search (§6.2), exact top-k
   build                          Dissimilarity Tree construction (§4.1)
+  insert                         incremental insertion (§4.1, reading R14)
   node_bound                     node lower bound (§4.2)
   tree_search                    best-first Dissimilarity Tree query (§4.2)
   permutation / retrieve         voting pipeline (§3)
@@ -64,6 +65,8 @@ def _load():
         lib.orc_bf_topk.restype = None
         lib.orc_build.argtypes = [P, i64, i32, i32, i32, P, P, P, P, P, P, P]
         lib.orc_build.restype = i64
+        lib.orc_insert.argtypes = [P, i64, i64, i32, i32, i64, P, P, P, P, P, P, P]
+        lib.orc_insert.restype = i64
         lib.orc_node_bound.argtypes = [P, P, P]
         lib.orc_node_bound.restype = i64
         lib.orc_tree_search.argtypes = [P, i64, P, P, P, P, P, P, P, i64, i32, P, P, P, P, i32]
@@ -176,6 +179,41 @@ def build(db, leaf_size=32, literal=False, with_and=False, nthreads=0):
     return Tree(child[:m].copy(), begin[:m].copy(), count[:m].copy(), level[:m].copy(),
                 or_img[:m].copy(), None if and_img is None else and_img[:m].copy(),
                 perm[:n].copy())
+
+
+def insert(db, tree: Tree, n_old, leaf_size=32, nthreads=0):
+    """Incremental insertion into a built tree (§4.1, reading R14).
+
+    ``db`` holds all descriptors by original index: rows 0 .. n_old-1 are the
+    ones ``tree`` indexes, rows n_old .. are the batch to insert.  AND images
+    are kept (and steer the routing) iff ``tree.and_img`` is not None.
+    Returns the new tree; ``tree`` is not modified.
+    """
+    db = _desc(db)
+    n = db.shape[0]
+    m = n - n_old
+    if m < 0 or tree.perm.shape[0] != n_old:
+        raise ValueError("db must hold the indexed descriptors followed by the batch")
+    nn = tree.n_nodes
+    cap = nn + 2 * n + 1
+    child = np.full((cap, 2), -1, dtype=np.int64)
+    begin = np.zeros(cap, dtype=np.int64)
+    count = np.zeros(cap, dtype=np.int64)
+    level = np.zeros(cap, dtype=np.int32)
+    or_img = np.zeros((cap, WORDS), dtype=np.uint64)
+    with_and = tree.and_img is not None
+    and_img = np.zeros((cap, WORDS), dtype=np.uint64) if with_and else None
+    perm = np.zeros(max(n, 1), dtype=np.int64)
+    child[:nn], begin[:nn], count[:nn], level[:nn] = tree.child, tree.begin, tree.count, tree.level
+    or_img[:nn] = tree.or_img
+    if with_and:
+        and_img[:nn] = tree.and_img
+    perm[:n_old] = tree.perm
+    total = _load().orc_insert(_p(db), n_old, m, leaf_size, _threads(nthreads), nn, _p(child),
+                               _p(begin), _p(count), _p(level), _p(or_img), _p(and_img), _p(perm))
+    return Tree(child[:total].copy(), begin[:total].copy(), count[:total].copy(),
+                level[:total].copy(), or_img[:total].copy(),
+                None if and_img is None else and_img[:total].copy(), perm[:n].copy())
 
 
 def node_bound(q, or_img, and_img=None):

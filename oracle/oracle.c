@@ -35,6 +35,16 @@
  *   R8  Results are ordered by (distance, original index) ascending.
  *   R10 "At random" in the voting loop of §3 is a Fisher-Yates permutation
  *       driven by SplitMix64; a vote goes to the object of the top-1 result.
+ *   R14 Incremental insertion, which §4.1 only suggests (redo the part of
+ *       the tree that new descriptors touch): a batch of new descriptors
+ *       takes indices n .. n+m-1; each descends, against the tree as it was before the batch, into the
+ *       child whose images it would widen least (bits set in it but not in
+ *       OR, plus bits clear in it but set in AND when AND images are kept;
+ *       the similar child on ties) — the least-enlargement rule of R-tree
+ *       insertion (Guttman, 1984); it joins that leaf after the leaf's old
+ *       descriptors; images become those of the enlarged sets; a leaf left
+ *       over leaf_size is rebuilt by §4.1 as a subtree root, new nodes
+ *       numbered from the old node count on, generation by generation.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -384,24 +394,21 @@ static void node_images(const uint64_t *db, const int64_t *list, int64_t n,
 }
 
 /*
- * Builds the tree one level at a time (breadth first); the recursion of the
- * listing visits the same nodes with the same splits, only in another
- * order.  The nodes of a level own disjoint segments of perm, so they are
- * split independently (OpenMP threads over a level's nodes); children are
- * then numbered in level order, similar child first.  literal != 0 selects
- * the bit-by-bit move loop, else the closed form.  Returns the node count.
+ * Splits the nodes of the work list cur[0..m) and all their descendants, one
+ * generation at a time: a node with more than leaf_size descriptors is split
+ * (closed form or literal move loop) and its two children are numbered from
+ * next_id on, in the order of their parents, similar child first; every
+ * processed node gets its segment, level and images.  The nodes of a
+ * generation own disjoint segments of perm, so they are split independently
+ * (OpenMP threads over the generation's nodes).  Returns the next free id.
  */
-int64_t orc_build(const uint64_t *db, int64_t n, int32_t leaf_size, int32_t literal,
-                  int32_t nthreads, int64_t *child, int64_t *begin, int64_t *count,
-                  int32_t *level, uint64_t *or_img, uint64_t *and_img, int64_t *perm)
+static int64_t grow(const uint64_t *db, int64_t *perm, work_t *cur, int64_t m, int64_t next_id,
+                    int64_t cap, int32_t leaf_size, int32_t literal, int32_t nthreads,
+                    int64_t *child, int64_t *begin, int64_t *count, int32_t *level,
+                    uint64_t *or_img, uint64_t *and_img)
 {
-    if (n <= 0) return 0;
-    for (int64_t i = 0; i < n; ++i) perm[i] = i;
-    work_t *cur = (work_t *)malloc(sizeof(work_t) * (size_t)(n + 1));
-    work_t *next = (work_t *)malloc(sizeof(work_t) * (size_t)(n + 1));
-    int64_t *n_sim = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
-    int64_t m = 1, next_id = 1;
-    cur[0] = (work_t){ 0, 0, n, 0 };
+    work_t *next = (work_t *)malloc(sizeof(work_t) * (size_t)(cap + 1));
+    int64_t *n_sim = (int64_t *)malloc(sizeof(int64_t) * (size_t)(cap + 1));
     int nt = nthreads > 0 ? nthreads : 1;
     while (m > 0) {
         /* few nodes: one at a time, each using all threads inside */
@@ -434,13 +441,138 @@ int64_t orc_build(const uint64_t *db, int64_t n, int32_t leaf_size, int32_t lite
             next[m2++] = (work_t){ s, w.begin, n_sim[i], w.level + 1 };
             next[m2++] = (work_t){ d, w.begin + n_sim[i], w.count - n_sim[i], w.level + 1 };
         }
-        work_t *t = cur; cur = next; next = t;
+        memcpy(cur, next, sizeof(work_t) * (size_t)m2);
         m = m2;
     }
     free(n_sim);
     free(next);
-    free(cur);
     return next_id;
+}
+
+/*
+ * Builds the tree one level at a time (breadth first) from the root; the
+ * recursion of the listing visits the same nodes with the same splits, only
+ * in another order.  literal != 0 selects the bit-by-bit move loop, else the
+ * closed form.  Returns the node count.
+ */
+int64_t orc_build(const uint64_t *db, int64_t n, int32_t leaf_size, int32_t literal,
+                  int32_t nthreads, int64_t *child, int64_t *begin, int64_t *count,
+                  int32_t *level, uint64_t *or_img, uint64_t *and_img, int64_t *perm)
+{
+    if (n <= 0) return 0;
+    for (int64_t i = 0; i < n; ++i) perm[i] = i;
+    work_t *cur = (work_t *)malloc(sizeof(work_t) * (size_t)(n + 1));
+    cur[0] = (work_t){ 0, 0, n, 0 };
+    int64_t n_nodes = grow(db, perm, cur, 1, 1, n, leaf_size, literal, nthreads,
+                           child, begin, count, level, or_img, and_img);
+    free(cur);
+    return n_nodes;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Incremental insertion (§4.1, reading R14)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* How much a node's images would widen if descriptor d joined it. */
+static int64_t growth(const uint64_t *d, const uint64_t *or_img, const uint64_t *and_img)
+{
+    int64_t g = 0;
+    for (int i = 0; i < OBITS; ++i) {
+        int db = get_bit(d, i);
+        if (db && !get_bit(or_img, i)) ++g;
+        if (and_img && !db && get_bit(and_img, i)) ++g;
+    }
+    return g;
+}
+
+/*
+ * Inserts descriptors n_old .. n_old+m-1 of db into a tree over descriptors
+ * 0 .. n_old-1 with n_nodes nodes (arrays as orc_build returns them, with
+ * room for n_nodes + 2 * (n_old + m) nodes and n_old + m perm entries).
+ *   1. every new descriptor descends from the root, against the tree as it
+ *      was before the batch, into the child whose images it widens least,
+ *      the similar child on ties, down to a leaf;
+ *   2. each leaf's segment becomes its old descriptors followed by those
+ *      routed to it in ascending index; leaves keep their order in perm and
+ *      every node's segment is the union of its leaves' segments;
+ *   3. every node's images are those of its new segment;
+ *   4. every leaf that now holds more than leaf_size descriptors, in
+ *      ascending id, is split again by the construction of §4.1 as the root
+ *      of a subtree; the new nodes get ids from n_nodes on, one generation at
+ *      a time over all those subtrees.
+ * Returns the new node count.
+ */
+int64_t orc_insert(const uint64_t *db, int64_t n_old, int64_t m, int32_t leaf_size, int32_t nthreads,
+                   int64_t n_nodes, int64_t *child, int64_t *begin, int64_t *count,
+                   int32_t *level, uint64_t *or_img, uint64_t *and_img, int64_t *perm)
+{
+    if (m <= 0) return n_nodes;
+    const int64_t n = n_old + m;
+    /* 1. routing */
+    int64_t *leaf_of = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    for (int64_t j = 0; j < m; ++j) {
+        const uint64_t *d = db + (n_old + j) * OW;
+        int64_t v = 0;
+        while (child[2 * v] >= 0) {
+            int64_t s = child[2 * v], t = child[2 * v + 1];
+            int64_t gs = growth(d, or_img + s * OW, and_img ? and_img + s * OW : NULL);
+            int64_t gt = growth(d, or_img + t * OW, and_img ? and_img + t * OW : NULL);
+            v = gs <= gt ? s : t;
+        }
+        leaf_of[j] = v;
+    }
+    /* 2. new segments: walk the leaves in perm order (depth first, similar
+     * child first), appending each leaf's new descriptors after its old ones */
+    int64_t *routed = (int64_t *)calloc((size_t)n_nodes + 1, sizeof(int64_t));
+    for (int64_t j = 0; j < m; ++j) routed[leaf_of[j] + 1]++;
+    for (int64_t v = 0; v < n_nodes; ++v) routed[v + 1] += routed[v];
+    int64_t *bucket = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    int64_t *fill = (int64_t *)calloc((size_t)n_nodes, sizeof(int64_t));
+    for (int64_t j = 0; j < m; ++j) bucket[routed[leaf_of[j]] + fill[leaf_of[j]]++] = n_old + j;
+    int64_t *old_perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_old);
+    memcpy(old_perm, perm, sizeof(int64_t) * (size_t)n_old);
+    int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n_nodes + 1));
+    int64_t sp = 0, pos = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        int64_t v = stack[--sp];
+        if (child[2 * v] >= 0) {
+            stack[sp++] = child[2 * v + 1];   /* dissimilar after similar */
+            stack[sp++] = child[2 * v];
+            continue;
+        }
+        int64_t b = pos;
+        for (int64_t i = 0; i < count[v]; ++i) perm[pos++] = old_perm[begin[v] + i];
+        for (int64_t i = routed[v]; i < routed[v + 1]; ++i) perm[pos++] = bucket[i];
+        begin[v] = b;
+        count[v] = pos - b;
+    }
+    /* children have larger ids than their parent: fill internal nodes last
+     * to first from their children */
+    for (int64_t v = n_nodes - 1; v >= 0; --v)
+        if (child[2 * v] >= 0) {
+            begin[v] = begin[child[2 * v]];
+            count[v] = count[child[2 * v]] + count[child[2 * v + 1]];
+        }
+    /* 3. images of the enlarged sets */
+    for (int64_t v = 0; v < n_nodes; ++v)
+        node_images(db, perm + begin[v], count[v], or_img + v * OW, and_img ? and_img + v * OW : NULL);
+    /* 4. overfull leaves become roots of rebuilt subtrees */
+    work_t *cur = (work_t *)malloc(sizeof(work_t) * (size_t)(n + 1));
+    int64_t n_roots = 0;
+    for (int64_t v = 0; v < n_nodes; ++v)
+        if (child[2 * v] < 0 && count[v] > leaf_size)
+            cur[n_roots++] = (work_t){ v, begin[v], count[v], level[v] };
+    int64_t total = grow(db, perm, cur, n_roots, n_nodes, n, leaf_size, 0, nthreads,
+                         child, begin, count, level, or_img, and_img);
+    free(cur);
+    free(stack);
+    free(old_perm);
+    free(fill);
+    free(bucket);
+    free(routed);
+    free(leaf_of);
+    return total;
 }
 
 /* ------------------------------------------------------------------------ */
