@@ -82,7 +82,7 @@ typedef struct {
 } dt_build_params;
 
 typedef struct {
-    int64_t n_nodes;        /* nodes, numbered breadth first */
+    int64_t n_nodes;        /* nodes; breadth first after dt_build (see dt_insert) */
     int64_t n_leaves;
     int32_t depth;          /* deepest level (root = 0) */
     int32_t leaf_size;
@@ -119,6 +119,35 @@ typedef struct {
  */
 int dt_build(const uint64_t *d_db, int64_t n, const dt_build_params *params, void *stream,
              dt_index **out);
+
+/*
+ * Incremental insertion.  §4.1 suggests that a tree can grow by redoing only
+ * the part that new descriptors touch; the rules below are this library's
+ * reading of that suggestion.  Appends the m descriptors d_new [m][64]
+ * (device, 16-byte aligned, not retained) to the index; they take original
+ * indices n .. n+m-1, n being the index's size before the call.
+ *   - Each new descriptor descends from the root into the child whose images
+ *     it widens least (its set bits outside the child's OR image, plus, with
+ *     AND images, its clear bits inside the child's AND image), the similar
+ *     child on ties, always against the tree as it was before the call.
+ *   - It joins that leaf after the leaf's descriptors (a leaf keeps
+ *     ascending original index), and every node on its path takes it into
+ *     its images.
+ *   - Every leaf left with more than leaf_size descriptors is split again by
+ *     dt_build's construction as the root of a new subtree.  New nodes are
+ *     numbered after the existing ones, one generation at a time over all
+ *     rebuilt subtrees (so the index is no longer numbered breadth first).
+ * Searches on the updated index stay exact.  Cost: one pass over the
+ * tree-ordered database (rows move to make room), O(m x depth) routing, and
+ * the rebuilt subtrees.  Synchronous: returns once the work on `stream` is
+ * complete.  The index must not be searched on another stream meanwhile,
+ * and the current device must be the one it was built on.  m == 0 is a
+ * no-op.
+ * Errors: DT_EINVAL (null index, m < 0, n + m > DT_MAX_N - 65536, null or
+ * misaligned d_new with m > 0, another current device), DT_ENOMEM, DT_ECUDA.
+ * On every error the index is left as it was.
+ */
+int dt_insert(dt_index *index, const uint64_t *d_new, int64_t m, void *stream);
 
 /* Shape of a built index (host call, no device work). */
 int dt_get_info(const dt_index *index, dt_index_info *info);

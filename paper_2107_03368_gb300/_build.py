@@ -27,6 +27,7 @@ CUDA_SOURCES = [
     "bf_popc.cu",
     "bf_tc.cu",
     "dt_build.cu",
+    "dt_insert.cu",
     "dt_search.cu",
     "encoder.cu",
     "enc_tc.cu",

@@ -139,6 +139,19 @@ int dt_build(const uint64_t *d_db, int64_t n, const dt_build_params *params, voi
     return DT_OK;
 }
 
+int dt_insert(dt_index *ix, const uint64_t *d_new, int64_t m, void *stream)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
+    DT_CHECK_ARG(m >= 0 && m <= DT_MAX_N - 65536 - ix->n, "m out of range");
+    if (m == 0) return DT_OK;
+    REQUIRE_DEV(d_new, "d_new");
+    int dev = -1;
+    DT_CUDA_TRY(cudaGetDevice(&dev));
+    DT_CHECK_ARG(dev == ix->device, "the current device must be the index's device");
+    return insert_tree(ix, d_new, m, (cudaStream_t)stream);
+}
+
 int dt_get_info(const dt_index *ix, dt_index_info *info)
 {
     DT_CHECK_ARG(ix && info, "index and info must not be NULL");

@@ -413,31 +413,6 @@ __global__ void iota_kernel(uint32_t *p, int64_t n)
     for (; i < n; i += stride) p[i] = (uint32_t)i;
 }
 
-// Device buffer that grows by doubling, keeping its contents.
-struct Grow {
-    void *p = nullptr;
-    size_t bytes = 0;
-    int ensure(size_t need, cudaStream_t s)
-    {
-        if (need <= bytes) return DT_OK;
-        size_t nb = std::max(need, bytes * 2);
-        void *q = nullptr;
-        DT_CUDA_TRY(dt_malloc_async(&q, nb, s));
-        if (p) {
-            DT_CUDA_TRY(cudaMemcpyAsync(q, p, bytes, cudaMemcpyDeviceToDevice, s));
-            DT_CUDA_TRY(cudaFreeAsync(p, s));
-        }
-        p = q;
-        bytes = nb;
-        return DT_OK;
-    }
-    void release(cudaStream_t s)
-    {
-        if (p) cudaFreeAsync(p, s);
-        p = nullptr;
-        bytes = 0;
-    }
-};
 
 size_t small_smem_bytes(int cap)
 {
@@ -446,8 +421,18 @@ size_t small_smem_bytes(int cap)
 
 }  // namespace
 
-int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fused_cap,
-               cudaStream_t s, dt_index *ix)
+// Splits every root and, level by level, all of its descendants (§4.1).
+// A root is a node whose descriptors occupy perm[begin, begin + count) in
+// ascending original-index order; perm holds row numbers of `db`.  Children
+// are numbered from recs.size() on, one level at a time, similar child
+// first, and appended to recs; recs[root.id] gets the root's segment and
+// first child.  Images of every processed node are written at its id in
+// g_or / g_and (grown as needed, contents kept).  Counts the processed
+// nodes that are leaves into *n_leaves and raises *depth to the deepest
+// level reached.
+int grow_forest(const uint64_t *db, uint32_t *perm, int64_t n_rows, const std::vector<BuildRoot> &roots,
+                int leaf_size, int use_and, int fused_cap, cudaStream_t s, Grow &g_or, Grow &g_and,
+                std::vector<NodeRec> &recs, int64_t *n_leaves, int32_t *depth)
 {
     int cap = fused_cap > 0 ? fused_cap : kDefaultCap;
     int p2 = 1;
@@ -463,24 +448,18 @@ int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fu
         set_error("fused_cap too large for shared memory");
         return DT_EINVAL;
     }
-    DT_CUDA_TRY(cudaFuncSetAttribute(small_node_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)ssmem));
+    DT_CUDA_TRY(allow_smem((const void *)small_node_kernel, ssmem));
 
     int rc = DT_OK;
-    uint32_t *perm = nullptr, *tmp = nullptr;
+    uint32_t *tmp = nullptr;
     uint64_t *mk = nullptr;
-    Grow g_or, g_and, g_work, g_chunks, g_counts, g_hist, g_kstar, g_mode, g_nsim, g_cdis, g_coff,
-        g_first;
-    std::vector<NodeRec> recs;
-    std::vector<int32_t> lvl_begin{0}, lvl_count{(int32_t)n};
-    int64_t base = 0;
-    int level = 0;
-    int64_t n_leaves = 0;
+    Grow g_work, g_chunks, g_counts, g_hist, g_kstar, g_mode, g_nsim, g_cdis, g_coff, g_first;
+    std::vector<BuildRoot> lvl(roots);
 
     auto cleanup = [&]() {
-        g_and.release(s); g_work.release(s); g_chunks.release(s); g_counts.release(s);
-        g_hist.release(s); g_kstar.release(s); g_mode.release(s); g_nsim.release(s);
-        g_cdis.release(s); g_coff.release(s); g_first.release(s);
+        g_work.release(s); g_chunks.release(s); g_counts.release(s); g_hist.release(s);
+        g_kstar.release(s); g_mode.release(s); g_nsim.release(s); g_cdis.release(s);
+        g_coff.release(s); g_first.release(s);
         if (tmp) cudaFreeAsync(tmp, s);
         if (mk) cudaFreeAsync(mk, s);
     };
@@ -503,42 +482,42 @@ int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fu
     } while (0)
 
     {
-        BUILD_CUDA(dt_malloc_async((void **)&perm, (size_t)n * 4, s));
-        BUILD_CUDA(dt_malloc_async((void **)&tmp, (size_t)n * 4, s));
-        BUILD_CUDA(dt_malloc_async((void **)&mk, (size_t)n * 8, s));
-        iota_kernel<<<std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(perm, n);
-        BUILD_CUDA(cudaGetLastError());
+        BUILD_CUDA(dt_malloc_async((void **)&tmp, (size_t)n_rows * 4, s));
+        BUILD_CUDA(dt_malloc_async((void **)&mk, (size_t)n_rows * 8, s));
 
         std::vector<NodeWork> small, large;
         std::vector<Chunk> chunks;
         std::vector<int32_t> first_chunk, n_sim;
-        while (!lvl_begin.empty()) {
-            const int64_t m = (int64_t)lvl_begin.size();
-            BUILD_TRY(g_or.ensure((size_t)(base + m) * kWords * 8, s));
-            if (use_and) BUILD_TRY(g_and.ensure((size_t)(base + m) * kWords * 8, s));
+        for (const BuildRoot &r : lvl) {
+            NodeRec &rec = recs[(size_t)r.id];
+            rec.first_child = -1;
+            rec.begin = r.begin;
+            rec.count = r.count;
+            rec.level = r.level;
+        }
+        while (!lvl.empty()) {
+            const int64_t m = (int64_t)lvl.size();
+            const size_t n_ids = recs.size();
+            BUILD_TRY(g_or.ensure(n_ids * kWords * 8, s));
+            if (use_and) BUILD_TRY(g_and.ensure(n_ids * kWords * 8, s));
             small.clear();
             large.clear();
             chunks.clear();
             first_chunk.clear();
             for (int64_t i = 0; i < m; ++i) {
-                NodeRec r;
-                r.first_child = -1;
-                r.begin = lvl_begin[i];
-                r.count = lvl_count[i];
-                r.level = level;
-                recs.push_back(r);
-                NodeWork w{(int32_t)(base + i), lvl_begin[i], lvl_count[i], (int32_t)i};
-                if (lvl_count[i] <= cap || lvl_count[i] <= leaf_size) {
+                const BuildRoot &r = lvl[(size_t)i];
+                NodeWork w{r.id, r.begin, r.count, (int32_t)i};
+                if (r.count <= cap || r.count <= leaf_size) {
                     small.push_back(w);
                 } else {
                     first_chunk.push_back((int32_t)chunks.size());
                     const int32_t slot = (int32_t)large.size();
-                    for (int32_t b = lvl_begin[i]; b < lvl_begin[i] + lvl_count[i]; b += CHUNK)
-                        chunks.push_back(Chunk{slot, b, std::min(b + CHUNK, lvl_begin[i] + lvl_count[i]),
-                                               lvl_begin[i]});
+                    for (int32_t b = r.begin; b < r.begin + r.count; b += CHUNK)
+                        chunks.push_back(Chunk{slot, b, std::min(b + CHUNK, r.begin + r.count), r.begin});
                     large.push_back(w);
                 }
-                if (lvl_count[i] <= leaf_size) ++n_leaves;
+                if (r.count <= leaf_size) ++*n_leaves;
+                *depth = std::max(*depth, r.level);
             }
             first_chunk.push_back((int32_t)chunks.size());
             BUILD_TRY(g_nsim.ensure((size_t)m * 4, s));
@@ -610,70 +589,89 @@ int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fu
             BUILD_CUDA(cudaStreamSynchronize(s));
 
             // next level: children of internal nodes, in order, similar first
-            std::vector<int32_t> nb, nc;
-            const int64_t next_base = base + m;
+            std::vector<BuildRoot> next;
             for (int64_t i = 0; i < m; ++i) {
-                if (lvl_count[i] <= leaf_size) continue;
+                const BuildRoot &r = lvl[(size_t)i];
+                if (r.count <= leaf_size) continue;
                 const int32_t ns = n_sim[(size_t)i];
-                if (ns <= 0 || ns >= lvl_count[i]) {
+                if (ns <= 0 || ns >= r.count) {
                     set_error("internal error: empty side after split");
                     rc = DT_ECUDA;
                     goto fail;
                 }
-                recs[(size_t)(base + i)].first_child = (int32_t)(next_base + (int64_t)nb.size());
-                nb.push_back(lvl_begin[i]);
-                nc.push_back(ns);
-                nb.push_back(lvl_begin[i] + ns);
-                nc.push_back(lvl_count[i] - ns);
+                const int32_t c0 = (int32_t)recs.size();
+                recs[(size_t)r.id].first_child = c0;
+                const BuildRoot sim{c0, r.begin, ns, r.level + 1};
+                const BuildRoot dis{c0 + 1, r.begin + ns, r.count - ns, r.level + 1};
+                for (const BuildRoot &c : {sim, dis}) {
+                    recs.push_back(NodeRec{-1, c.begin, c.count, c.level});
+                    next.push_back(c);
+                }
             }
-            base = next_base;
-            lvl_begin.swap(nb);
-            lvl_count.swap(nc);
-            if (!lvl_begin.empty()) ++level;
+            lvl.swap(next);
         }
-
-        // finalize the index
-        ix->n = n;
-        ix->n_nodes = base;
-        ix->n_leaves = n_leaves;
-        ix->depth = level;
-        ix->leaf_size = leaf_size;
-        ix->use_and = use_and;
-        BUILD_CUDA(cudaMalloc((void **)&ix->or_img, (size_t)base * kWords * 8));
-        BUILD_CUDA(cudaMemcpyAsync(ix->or_img, g_or.p, (size_t)base * kWords * 8,
-                                   cudaMemcpyDeviceToDevice, s));
-        if (use_and) {
-            BUILD_CUDA(cudaMalloc((void **)&ix->and_img, (size_t)base * kWords * 8));
-            BUILD_CUDA(cudaMemcpyAsync(ix->and_img, g_and.p, (size_t)base * kWords * 8,
-                                       cudaMemcpyDeviceToDevice, s));
-        }
-        BUILD_CUDA(cudaMalloc((void **)&ix->node, (size_t)base * sizeof(NodeRec)));
-        BUILD_CUDA(cudaMemcpyAsync(ix->node, recs.data(), (size_t)base * sizeof(NodeRec),
-                                   cudaMemcpyHostToDevice, s));
-        BUILD_CUDA(cudaMalloc((void **)&ix->db_tree, (size_t)n * kWords * 8));
-        BUILD_CUDA(cudaMalloc((void **)&ix->perm, (size_t)n * 4));
-        gather_rows_kernel<<<std::min<int64_t>((n + 7) / 8, 8 * 152 * 8), 256, 0, s>>>(db, perm, n,
-                                                                                       ix->db_tree);
-        BUILD_CUDA(cudaGetLastError());
-        BUILD_CUDA(cudaMemcpyAsync(ix->perm, perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-        BUILD_CUDA(cudaMalloc((void **)&ix->iperm, (size_t)n * 4));
-        invert_kernel<<<std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(perm, n, ix->iperm);
-        BUILD_CUDA(cudaGetLastError());
         cleanup();
-        g_or.release(s);
-        cudaFreeAsync(perm, s);
-        perm = nullptr;
-        BUILD_CUDA(cudaStreamSynchronize(s));
         return DT_OK;
     }
 fail:
     cleanup();
-    g_or.release(s);
-    if (perm) cudaFreeAsync(perm, s);
     cudaStreamSynchronize(s);
     return rc;
 #undef BUILD_TRY
 #undef BUILD_CUDA
+}
+
+int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fused_cap,
+               cudaStream_t s, dt_index *ix)
+{
+    Scratch scratch(s);
+    uint32_t *perm = nullptr;
+    DT_CUDA_TRY(scratch.alloc(&perm, (size_t)n * 4));
+    iota_kernel<<<std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(perm, n);
+    DT_CUDA_TRY(cudaGetLastError());
+
+    Grow g_or, g_and;
+    struct Release {
+        Grow &a, &b;
+        cudaStream_t s;
+        ~Release() { a.release(s); b.release(s); }
+    } release{g_or, g_and, s};
+    std::vector<NodeRec> recs{NodeRec{-1, 0, (int32_t)n, 0}};
+    int64_t n_leaves = 0;
+    int32_t depth = 0;
+    int rc = grow_forest(db, perm, n, {BuildRoot{0, 0, (int32_t)n, 0}}, leaf_size, use_and, fused_cap,
+                         s, g_or, g_and, recs, &n_leaves, &depth);
+    if (rc != DT_OK) return rc;
+
+    const int64_t n_nodes = (int64_t)recs.size();
+    ix->n = n;
+    ix->n_nodes = n_nodes;
+    ix->n_leaves = n_leaves;
+    ix->depth = depth;
+    ix->leaf_size = leaf_size;
+    ix->use_and = use_and;
+    DT_CUDA_TRY(cudaMalloc((void **)&ix->or_img, (size_t)n_nodes * kWords * 8));
+    DT_CUDA_TRY(cudaMemcpyAsync(ix->or_img, g_or.p, (size_t)n_nodes * kWords * 8,
+                                cudaMemcpyDeviceToDevice, s));
+    if (use_and) {
+        DT_CUDA_TRY(cudaMalloc((void **)&ix->and_img, (size_t)n_nodes * kWords * 8));
+        DT_CUDA_TRY(cudaMemcpyAsync(ix->and_img, g_and.p, (size_t)n_nodes * kWords * 8,
+                                    cudaMemcpyDeviceToDevice, s));
+    }
+    DT_CUDA_TRY(cudaMalloc((void **)&ix->node, (size_t)n_nodes * sizeof(NodeRec)));
+    DT_CUDA_TRY(cudaMemcpyAsync(ix->node, recs.data(), (size_t)n_nodes * sizeof(NodeRec),
+                                cudaMemcpyHostToDevice, s));
+    DT_CUDA_TRY(cudaMalloc((void **)&ix->db_tree, (size_t)n * kWords * 8));
+    DT_CUDA_TRY(cudaMalloc((void **)&ix->perm, (size_t)n * 4));
+    DT_CUDA_TRY(cudaMalloc((void **)&ix->iperm, (size_t)n * 4));
+    gather_rows_kernel<<<std::min<int64_t>((n + 7) / 8, 8 * 152 * 8), 256, 0, s>>>(db, perm, n,
+                                                                                   ix->db_tree);
+    DT_CUDA_TRY(cudaGetLastError());
+    DT_CUDA_TRY(cudaMemcpyAsync(ix->perm, perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    invert_kernel<<<std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(perm, n, ix->iperm);
+    DT_CUDA_TRY(cudaGetLastError());
+    DT_CUDA_TRY(cudaStreamSynchronize(s));
+    return DT_OK;
 }
 
 }  // namespace dtk

@@ -3,7 +3,9 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <string>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "dt.h"
@@ -162,6 +164,32 @@ class Scratch {
     int n_ = 0;
 };
 
+// Device buffer that grows by doubling, keeping its contents.
+struct Grow {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t need, cudaStream_t s)
+    {
+        if (need <= bytes) return DT_OK;
+        size_t nb = std::max(need, bytes * 2);
+        void *q = nullptr;
+        DT_CUDA_TRY(dt_malloc_async(&q, nb, s));
+        if (p) {
+            DT_CUDA_TRY(cudaMemcpyAsync(q, p, bytes, cudaMemcpyDeviceToDevice, s));
+            DT_CUDA_TRY(cudaFreeAsync(p, s));
+        }
+        p = q;
+        bytes = nb;
+        return DT_OK;
+    }
+    void release(cudaStream_t s)
+    {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
 int sm_count();
 
 // Let `func` use `bytes` of dynamic shared memory on the current device (a
@@ -236,6 +264,14 @@ int launch_bf_popc(const uint64_t *db, int64_t n, const uint64_t *q, int64_t nq,
                    uint32_t *idx, float *score, uint16_t *ab, cudaStream_t s);
 int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fused_cap,
                cudaStream_t s, dt_index *ix);
+// A node to split with all of its descendants (tree construction, §4.1).
+struct BuildRoot {
+    int32_t id, begin, count, level;
+};
+int grow_forest(const uint64_t *db, uint32_t *perm, int64_t n_rows, const std::vector<BuildRoot> &roots,
+                int leaf_size, int use_and, int fused_cap, cudaStream_t s, Grow &g_or, Grow &g_and,
+                std::vector<NodeRec> &recs, int64_t *n_leaves, int32_t *depth);
+int insert_tree(dt_index *ix, const uint64_t *d_new, int64_t m, cudaStream_t s);
 int launch_dt_search(const dt_index *ix, const uint64_t *q, int64_t nq, int k, uint32_t *idx,
                      float *score, uint16_t *ab, dt_stats *stats, cudaStream_t s);
 int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects,

@@ -74,6 +74,7 @@ def load():
         P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
         sig = {
             "dt_build": ([P, i64, P, P, P], ctypes.c_int),
+            "dt_insert": ([P, P, i64, P], ctypes.c_int),
             "dt_get_info": ([P, P], ctypes.c_int),
             "dt_export": ([P, P, P, P, P, P, P, P], ctypes.c_int),
             "dt_search": ([P, P, i64, i32, P, P, P, P, P], ctypes.c_int),
@@ -177,6 +178,14 @@ def dt_build(db, leaf_size=32, use_and_image=False, fused_cap=0, stream=None) ->
     _check(load().dt_build(_ptr(db), db.shape[0], ctypes.byref(params), _stream(stream),
                            ctypes.byref(out)), "dt_build")
     return Index(out)
+
+
+def dt_insert(index: Index, new, stream=None) -> Index:
+    """Appends the descriptors ``new`` [m, 64] (device) to ``index`` in place;
+    they take original indices n .. n+m-1.  Returns ``index``."""
+    new = _desc(new, "new")
+    _check(load().dt_insert(index.handle, _ptr(new), new.shape[0], _stream(stream)), "dt_insert")
+    return index
 
 
 def _outputs(nq, k, device, with_ab, out):

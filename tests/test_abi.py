@@ -60,7 +60,7 @@ def test_bad_sizes_are_rejected():
 
 
 def test_new_entry_points_check_their_arguments_first():
-    """Warm-started search, inverted-file search and embedding reject bad
+    """Warm-started search, inverted-file search, embedding and insertion reject bad
     arguments with DT_EINVAL before touching the device."""
     from paper_2107_03368_gb300 import learned
     lib = learned._lib()
@@ -73,6 +73,7 @@ def test_new_entry_points_check_their_arguments_first():
     assert "n_seed" in dt.dt_last_error()
     assert lib.ivf_search(None, None, None, 5, 1, 1, None, None, None, 0, None) == dt.DT_EINVAL
     assert lib.enc_embed(None, None, 5, None, None, 0, None) == dt.DT_EINVAL
+    assert dt.load().dt_insert(None, None, 5, None) == dt.DT_EINVAL
 
 
 def test_tune_table_file_roundtrip(tmp_path):
