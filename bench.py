@@ -60,6 +60,8 @@ def parse_args(argv=None):
     p.add_argument("--target-recall", type=float, default=0.99)
     p.add_argument("--untrained-baseline", type=int, default=1,
                    help="also sweep the encoder at its initial weights (1/0)")
+    p.add_argument("--insert-n", type=int, default=100_000,
+                   help="descriptors of new objects inserted into the tree (0: skip)")
     p.add_argument("--workload", choices=["tree", "tensor-bf"], default="tree",
                    help="tree: the tree-search step (default); tensor-bf: the large-batch "
                         "brute force, 65,536 queries x 20,000,000 descriptors")
@@ -422,6 +424,8 @@ def run_ours(a, dist):
     if not a.no_learned:
         line["learned"] = learned_leg(a, dist, d_db, d_q, db, value / dist.world, bf_best, stream,
                                       ix, tree_idx)
+    if a.insert_n > 0:                # last: it grows the index
+        line["insert"] = insert_leg(a, ix, d_db, d_q, build_s, stream, nt)
 
     # roofline of the dominant kernel (dt_search): algorithmic bytes per query =
     # 512 B x (bounds evaluated + descriptors scanned) of the oracle's best-first
@@ -448,6 +452,62 @@ def run_ours(a, dist):
         print(json.dumps(line), flush=True)
     ix.free()
     return 0
+
+
+def insert_leg(a, ix, d_db, d_q, build_s, stream, nt):
+    """Incremental insertion: descriptors of new objects go into the built
+    tree.  A slice of the batch's queries is searched before and after (the
+    same queries), and the result after is checked against the tensor-core
+    brute force over all descriptors."""
+    import torch
+    from paper_2107_03368_gb300 import dt, synth
+
+    nq = min(a.nq, 2000)
+    k = a.k
+    dq = d_q[:nq].contiguous()
+
+    def timed_search():
+        dt.dt_search(ix, dq, k)             # warm-up
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        idx, score, _, _ = dt.dt_search(ix, dq, k)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return nq / (s0.elapsed_time(s1) / 1e3), idx, score
+
+    qps_before, _, _ = timed_search()
+    new, _ = synth.database(SEED + 77, a.insert_n, per_object=a.per_object, nthreads=nt)
+    d_new = torch.from_numpy(new.view(np.int64)).to(d_db.device)
+    before = ix.info()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    with nvtx("insert"):
+        dt.dt_insert(ix, d_new)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ev_s = e0.elapsed_time(e1) / 1e3
+    after = ix.info()
+
+    qps_after, t_idx, t_score = timed_search()
+    d_all = torch.cat([d_db, d_new])
+    c_idx, c_score, _ = dt.bf_search(d_all, dq, k, path=2)
+    same = bool(torch.equal(t_idx, c_idx) and torch.equal(t_score, c_score))
+    del d_all
+    rows_moved = before["n"] + a.insert_n
+    return {"inserted": a.insert_n, "n_before": before["n"], "n_after": after["n"],
+            "seconds": wall, "seconds_cuda_events": ev_s,
+            "descriptors_per_s": a.insert_n / wall,
+            "full_build_s_before": build_s, "vs_full_build": wall / build_s,
+            "nodes_before": before["n_nodes"], "nodes_after": after["n_nodes"],
+            "depth_before": before["depth"], "depth_after": after["depth"],
+            "tree_bytes_moved_per_s": rows_moved * 516 * 2 / wall,
+            "search": {"queries": nq, "queries_per_s_before": qps_before,
+                       "queries_per_s_after": qps_after,
+                       "after_same_as_tensor_bf_over_all": same}}
 
 
 def graph_replay_leg(fn, result, ref, stream):

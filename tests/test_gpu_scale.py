@@ -4,6 +4,11 @@
   benchmark's configuration): dt_search equals bf_search for every query
   (indices, (A, B) counts, scores), and a spread sample of queries equals the
   oracle's exact top-10; sampled tree nodes satisfy the structural facts.
+- Incremental insertion at scale: 100,000 descriptors of new objects go into
+  a 10,000,000-descriptor tree; tree search over the grown tree equals the
+  tensor-core brute force over all 10,100,000 descriptors for every query
+  (old and new objects), sampled queries equal the oracle, and sampled
+  nodes (old and rebuilt) cover exactly their members.
 - Partial-object retrieval on the 400-object x 25,000-descriptor database:
   votes equal the histogram of the brute-force nearest neighbours' objects
   (a separate GPU path) for a subset of uneven partial queries, and sampled
@@ -72,6 +77,46 @@ def test_sampled_nodes_structure(big):
             assert c > 32
             assert t["begin"][s] == b and t["begin"][d] == b + t["count"][s]
             assert t["count"][s] + t["count"][d] == c and t["count"][s] > 0
+
+
+def test_insert_at_full_size(big):
+    db, q, d_db, d_q, _ = big
+    new, _ = synth.database(SEED + 5, 100_000, per_object=1000)
+    q_new, _ = synth.queries(SEED + 6, new, 1000)
+    ix = dt.dt_build(d_db)
+    try:
+        n_nodes0 = ix.info()["n_nodes"]
+        dt.dt_insert(ix, to_dev(new))
+        info = ix.info()
+        assert info["n"] == 10_100_000 and info["n_nodes"] > n_nodes0
+        all_db = np.concatenate([db, new])
+        d_all = torch.cat([d_db, to_dev(new)])
+        qq = np.concatenate([q, q_new])
+        d_qq = to_dev(qq)
+        t_idx, t_score, t_ab, _ = dt.dt_search(ix, d_qq, 10, with_ab=True)
+        c_idx, c_score, c_ab = dt.bf_search(d_all, d_qq, 10, with_ab=True, path=2)
+        dt.dt_sync_status()
+        assert torch.equal(t_idx, c_idx) and torch.equal(t_ab, c_ab) and torch.equal(t_score, c_score)
+        hit_new = (idx_np(t_idx)[:, 0] >= 10_000_000).mean()
+        assert hit_new > 0.05                    # the new objects' queries find them
+        pick = np.concatenate([np.linspace(0, 9999, 6), np.linspace(10000, 10999, 6)]).astype(np.int64)
+        o_idx, o_score, o_ab = oracle.bf_topk(all_db, qq[pick], 10)
+        assert np.array_equal(idx_np(t_idx)[pick], o_idx)
+        assert np.array_equal(u16_np(t_ab)[pick], o_ab)
+        np.testing.assert_allclose(t_score.cpu().numpy()[pick], o_score, rtol=SCORE_RTOL, atol=0)
+        t = ix.export()
+        assert sorted(t["perm"][-1000:].tolist()) == sorted(set(t["perm"][-1000:].tolist()))
+        rng = np.random.default_rng(1)
+        nodes = np.concatenate([rng.integers(0, n_nodes0, 100),
+                                rng.integers(n_nodes0, info["n_nodes"], 100)])
+        for node in nodes:
+            b, c = t["begin"][node], t["count"][node]
+            mem = t["perm"][b:b + c]
+            assert np.array_equal(np.bitwise_or.reduce(all_db[mem], axis=0), t["or_img"][node])
+            if t["child"][node][0] < 0:
+                assert c <= 32 and np.all(np.diff(mem) > 0)
+    finally:
+        ix.free()
 
 
 def test_partial_retrieval_on_full_database():
