@@ -10,6 +10,7 @@ Functions and the passages they follow:
   bf_topk                        sequential search (§6.2), exact top-k
   build                          Dissimilarity Tree construction (§4.1)
   insert                         incremental insertion (§4.1, reading R14)
+  quicci                         QUICCI and modified QUICCI generation (§2.2, §5, R15)
   node_bound                     node lower bound (§4.2)
   tree_search                    best-first Dissimilarity Tree query (§4.2)
   permutation / retrieve         voting pipeline (§3)
@@ -67,6 +68,8 @@ def _load():
         lib.orc_build.restype = i64
         lib.orc_insert.argtypes = [P, i64, i64, i32, i32, i64, P, P, P, P, P, P, P]
         lib.orc_insert.restype = i64
+        lib.orc_quicci.argtypes = [P, i64, P, i64, P, P, i64, f64, i32, i32, P]
+        lib.orc_quicci.restype = None
         lib.orc_node_bound.argtypes = [P, P, P]
         lib.orc_node_bound.restype = i64
         lib.orc_tree_search.argtypes = [P, i64, P, P, P, P, P, P, P, i64, i32, P, P, P, P, i32]
@@ -287,3 +290,24 @@ def object_scores(db, object_of, n_objects, qdesc, offsets, nthreads=0):
     _load().orc_object_scores(_p(db), db.shape[0], _p(obj), n_objects, _p(qdesc), _p(off), nq,
                               _p(out), _threads(nthreads))
     return out
+
+
+def quicci(vertices, triangles, points, normals, support_radius=100.0, modified=False,
+           nthreads=0):
+    """One 64x64-bit QUICCI (or modified QUICCI) per oriented point, counted
+    circle by circle in FP64 (§2.2, §5, reading R15).  vertices float [nv, 3],
+    triangles int [nt, 3], points / normals float [np, 3]; returns uint64
+    [np, 64] (word = layer from the bottom, bit = circle from the innermost)."""
+    v = np.ascontiguousarray(vertices, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(triangles, dtype=np.int32).reshape(-1, 3)
+    p = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+    n = np.ascontiguousarray(normals, dtype=np.float32).reshape(-1, 3)
+    if p.shape != n.shape:
+        raise ValueError("points and normals must match")
+    if t.size and (t.min() < 0 or t.max() >= v.shape[0]):
+        raise ValueError("triangle vertex id out of range")
+    out = np.zeros((p.shape[0], WORDS), dtype=np.uint64)
+    _load().orc_quicci(_p(v), v.shape[0], _p(t), t.shape[0], _p(p), _p(n), p.shape[0],
+                       float(support_radius), 1 if modified else 0, _threads(nthreads), _p(out))
+    return out
+

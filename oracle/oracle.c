@@ -35,6 +35,20 @@
  *   R8  Results are ordered by (distance, original index) ascending.
  *   R10 "At random" in the voting loop of §3 is a Fisher-Yates permutation
  *       driven by SplitMix64; a vote goes to the object of the top-1 result.
+ *   R15 QUICCI geometry (§2.2 describes it in words only): the oriented
+ *       point p with unit normal n (normalised here; a zero normal gives an
+ *       empty descriptor) is the axis of N = 64 layers and N circles per
+ *       layer.  Layer l (word l, bottom = 0) is the plane at height
+ *       z_l = -R + (2l + 1) R / N along n, so the layers evenly fill
+ *       [-R, R] around p; circle c (bit c) has radius r_c = (c + 1) R / N,
+ *       so the largest is the support radius R; the circle one step smaller
+ *       than c = 0 has radius 0 and meets nothing.  A circle's
+ *       intersection count is the number of points where it meets the
+ *       mesh's triangles; a layer plane cuts a triangle in a segment when
+ *       some vertex lies below it (height < z_l) and some not.  Bit (l, c)
+ *       is set iff the count of circle c differs from that of circle c-1;
+ *       the modified QUICCI of §5 sets it only if the two differ by 2 or
+ *       more.
  *   R14 Incremental insertion, which §4.1 only suggests (redo the part of
  *       the tree that new descriptors touch): a batch of new descriptors
  *       takes indices n .. n+m-1; each descends, against the tree as it was before the batch, into the
@@ -819,5 +833,94 @@ void orc_object_scores(const uint64_t *db, int64_t n, const uint32_t *object_of,
             for (int32_t o = 0; o < n_objects; ++o) row[o] += best[o];
         }
         free(best);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* QUICCI (§2.2) and the modified QUICCI for partial queries (§5), R15      */
+/* ------------------------------------------------------------------------ */
+
+#define QN 64          /* layers and circles per layer */
+
+/* Number of points where the circle of radius r about the axis meets the
+ * segment a + t (b - a), t in [0, 1]; a and b are offsets from the axis
+ * within one layer plane.  A tangent point counts once. */
+static int circle_hits(const double *a, const double *b, double r)
+{
+    double d[3] = { b[0] - a[0], b[1] - a[1], b[2] - a[2] };
+    double qa = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double qb = 2.0 * (a[0] * d[0] + a[1] * d[1] + a[2] * d[2]);
+    double qc = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] - r * r;
+    if (qa == 0.0) return qc == 0.0;          /* a single point */
+    double disc = qb * qb - 4.0 * qa * qc;
+    if (disc < 0.0) return 0;
+    double sq = sqrt(disc);
+    double t1 = (-qb - sq) / (2.0 * qa), t2 = (-qb + sq) / (2.0 * qa);
+    int hits = (t1 >= 0.0 && t1 <= 1.0);
+    if (disc > 0.0) hits += (t2 >= 0.0 && t2 <= 1.0);
+    return hits;
+}
+
+/*
+ * One 64x64-bit QUICCI per oriented point (points[j], normals[j]) of the
+ * mesh (vertices [nv][3], triangles [nt][3] vertex ids), support radius R;
+ * modified != 0 gives the modified QUICCI.  out [np][64]: word l = layer l,
+ * bit c = circle c (reading R11).  Counts every circle's intersections with
+ * every triangle in FP64.
+ */
+void orc_quicci(const float *vertices, int64_t nv, const int32_t *tris, int64_t nt,
+                const float *points, const float *normals, int64_t np, double R,
+                int32_t modified, int32_t nthreads, uint64_t *out)
+{
+    (void)nv;
+    int nth = nthreads > 0 ? nthreads : 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth)
+    for (int64_t j = 0; j < np; ++j) {
+        uint64_t *img = out + j * OW;
+        memset(img, 0, sizeof(uint64_t) * OW);
+        double p[3], n[3], len = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            p[k] = points[j * 3 + k];
+            n[k] = normals[j * 3 + k];
+            len += n[k] * n[k];
+        }
+        if (len == 0.0) continue;
+        len = sqrt(len);
+        for (int k = 0; k < 3; ++k) n[k] /= len;
+        int64_t *cnt = (int64_t *)calloc(QN * QN, sizeof(int64_t));
+        for (int64_t t = 0; t < nt; ++t) {
+            double z[3], q[3][3];
+            for (int i = 0; i < 3; ++i) {
+                const float *v = vertices + (int64_t)tris[t * 3 + i] * 3;
+                double rel[3] = { v[0] - p[0], v[1] - p[1], v[2] - p[2] };
+                z[i] = rel[0] * n[0] + rel[1] * n[1] + rel[2] * n[2];
+                for (int k = 0; k < 3; ++k) q[i][k] = rel[k] - z[i] * n[k];
+            }
+            for (int l = 0; l < QN; ++l) {
+                double zl = -R + (2.0 * l + 1.0) * R / QN;
+                int below[3], nb = 0;
+                for (int i = 0; i < 3; ++i) nb += below[i] = z[i] < zl;
+                if (nb == 0 || nb == 3) continue;
+                double seg[2][3];
+                int ns = 0;
+                for (int e = 0; e < 3; ++e) {
+                    int a = e, b = (e + 1) % 3;
+                    if (below[a] == below[b]) continue;
+                    double s = (zl - z[a]) / (z[b] - z[a]);
+                    for (int k = 0; k < 3; ++k) seg[ns][k] = q[a][k] + s * (q[b][k] - q[a][k]);
+                    ++ns;
+                }
+                for (int c = 0; c < QN; ++c)
+                    cnt[l * QN + c] += circle_hits(seg[0], seg[1], (c + 1.0) * R / QN);
+            }
+        }
+        for (int l = 0; l < QN; ++l)
+            for (int c = 0; c < QN; ++c) {
+                int64_t prev = c > 0 ? cnt[l * QN + c - 1] : 0;
+                int64_t d = cnt[l * QN + c] - prev;
+                int set = modified ? (d >= 2 || d <= -2) : (d != 0);
+                if (set) img[l] |= 1ULL << c;
+            }
+        free(cnt);
     }
 }

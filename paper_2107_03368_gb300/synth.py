@@ -111,3 +111,96 @@ def workload_small():
     db, obj = database(seed, 100_000, per_object=1000)
     q, src = queries(seed, db, 100)
     return dict(seed=seed, db=db, object_of=obj, q=q, src=src)
+
+
+# --- Synthetic meshes (QUICCI generation inputs) ---------------------------
+#
+# SHREC'16's scanned objects are not available; these stand in for them:
+# closed, smooth, blob-shaped triangle meshes (an icosphere whose radius is
+# modulated by a few random waves), and partial views of them made of the
+# triangles that face a random viewing direction (no occlusion test).  Units
+# follow the paper's support radius of 100: objects are a few hundred units
+# across.  Vertex normals are area-weighted averages of the incident faces.
+
+
+def _icosphere(subdiv: int):
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+         (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    verts = [np.array(x, dtype=np.float64) / np.linalg.norm(x) for x in v]
+    faces = f
+    for _ in range(subdiv):
+        mid = {}
+
+        def midpoint(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                mid[key] = len(verts) - 1
+            return mid[key]
+
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    return np.array(verts), np.array(faces, dtype=np.int64)
+
+
+_ICO = {}
+
+
+def vertex_normals(vertices: np.ndarray, triangles: np.ndarray) -> np.ndarray:
+    """Area-weighted average of the incident faces' normals, unit length."""
+    v = vertices.astype(np.float64)
+    fn = np.cross(v[triangles[:, 1]] - v[triangles[:, 0]], v[triangles[:, 2]] - v[triangles[:, 0]])
+    n = np.zeros_like(v)
+    for k in range(3):
+        np.add.at(n, triangles[:, k], fn)
+    ln = np.linalg.norm(n, axis=1, keepdims=True)
+    return (n / np.where(ln > 0, ln, 1.0)).astype(np.float32)
+
+
+def mesh_object(seed: int, subdiv: int = 4, radius: float = 150.0):
+    """A closed blob: returns (vertices float32 [nv, 3], triangles int32
+    [nt, 3], vertex normals float32 [nv, 3]).  subdiv 4 gives 2,562 vertices
+    and 5,120 triangles; each step multiplies both by about four."""
+    if subdiv not in _ICO:
+        _ICO[subdiv] = _icosphere(subdiv)
+    unit, faces = _ICO[subdiv]
+    rng = np.random.default_rng(seed)
+    r = np.ones(unit.shape[0])
+    for _ in range(6):
+        axis = rng.normal(size=3)
+        axis /= np.linalg.norm(axis)
+        freq = rng.uniform(1.0, 4.0)
+        r += rng.uniform(0.05, 0.25) * np.sin(freq * unit @ axis + rng.uniform(0, 2 * np.pi))
+    stretch = rng.uniform(0.6, 1.4, size=3)
+    v = unit * (radius * r)[:, None] * stretch[None, :]
+    v = v + rng.uniform(-50, 50, size=3)
+    verts = v.astype(np.float32)
+    tris = faces.astype(np.int32)
+    return verts, tris, vertex_normals(verts, tris)
+
+
+def mesh_partial(seed: int, vertices: np.ndarray, triangles: np.ndarray):
+    """The triangles facing a random viewing direction, as a mesh of its own
+    (vertices renumbered, normals from the kept faces); returns (vertices,
+    triangles, normals, kept vertex ids in the complete mesh)."""
+    rng = np.random.default_rng(seed)
+    view = rng.normal(size=3)
+    view /= np.linalg.norm(view)
+    v = vertices.astype(np.float64)
+    fn = np.cross(v[triangles[:, 1]] - v[triangles[:, 0]], v[triangles[:, 2]] - v[triangles[:, 0]])
+    keep = fn @ view > 0
+    tris = triangles[keep]
+    used = np.unique(tris)
+    remap = np.full(vertices.shape[0], -1, np.int64)
+    remap[used] = np.arange(used.size)
+    pv = vertices[used].copy()
+    pt = remap[tris].astype(np.int32)
+    return pv, pt, vertex_normals(pv, pt), used
