@@ -149,6 +149,37 @@ int dt_build(const uint64_t *d_db, int64_t n, const dt_build_params *params, voi
  */
 int dt_insert(dt_index *index, const uint64_t *d_new, int64_t m, void *stream);
 
+/*
+ * QUICCI descriptors (§2.2) of oriented points on a triangle mesh, or the
+ * modified QUICCI of §5 for partial query meshes (modified != 0).  Bit
+ * (layer l, circle c) — bit c of word l of a point's 64 words — is set iff
+ * the number of points where circle c meets the mesh differs from that of
+ * circle c - 1, by at least 2 when modified (boundaries of a partial mesh
+ * change counts by 1, closed surfaces by 2).  Geometry (this library's
+ * reading; the paper describes it in words): the point's normal,
+ * normalised (a zero normal gives an empty descriptor), is the axis; layer
+ * l is the plane at height -R + (2l + 1) R / 64 along it, so the layers
+ * evenly fill [-R, R]; circle c has radius (c + 1) R / 64, circle -1 radius
+ * 0.  A layer plane cuts a triangle when some vertex lies below it (height
+ * < the plane's) and some does not.
+ * d_vertices [n_vertices][3] float, d_triangles [n_triangles][3] int32
+ * vertex ids, d_points and d_normals [n_points][3] float, all device
+ * memory; d_out [n_points][64] uint64 (device, 16-byte aligned).  FP32
+ * arithmetic: a bit can differ from exact arithmetic only where a circle
+ * passes within rounding distance of a segment's end or closest point, or a
+ * layer plane within rounding distance of a vertex.  Every triangle is
+ * tested against every point (bounding-sphere rejection first).  Waits on
+ * the host once, to validate the triangles' vertex ids, then enqueues the
+ * descriptor kernel on `stream`.
+ * Errors: DT_EINVAL (null or misaligned pointers, negative or too large
+ * sizes, triangles without vertices, support_radius not positive and
+ * finite, a vertex id outside [0, n_vertices)), DT_ENOMEM, DT_ECUDA.
+ */
+int quicci_generate(const float *d_vertices, int64_t n_vertices, const int32_t *d_triangles,
+                    int64_t n_triangles, const float *d_points, const float *d_normals,
+                    int64_t n_points, float support_radius, int32_t modified, uint64_t *d_out,
+                    void *stream);
+
 /* Shape of a built index (host call, no device work). */
 int dt_get_info(const dt_index *index, dt_index_info *info);
 

@@ -1,6 +1,7 @@
 // api.cu — the C ABI of include/dt.h: argument checks, index lifetime and
 // dispatch to the kernel launchers.  No computation happens here.
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -150,6 +151,30 @@ int dt_insert(dt_index *ix, const uint64_t *d_new, int64_t m, void *stream)
     DT_CUDA_TRY(cudaGetDevice(&dev));
     DT_CHECK_ARG(dev == ix->device, "the current device must be the index's device");
     return insert_tree(ix, d_new, m, (cudaStream_t)stream);
+}
+
+int quicci_generate(const float *d_vertices, int64_t n_vertices, const int32_t *d_triangles,
+                    int64_t n_triangles, const float *d_points, const float *d_normals,
+                    int64_t n_points, float support_radius, int32_t modified, uint64_t *d_out,
+                    void *stream)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(n_vertices >= 0 && n_vertices <= 2147483647LL, "n_vertices out of range");
+    DT_CHECK_ARG(n_triangles >= 0 && n_triangles <= 2147483647LL, "n_triangles out of range");
+    DT_CHECK_ARG(n_points >= 0 && n_points < (1LL << 40), "n_points out of range");
+    DT_CHECK_ARG(support_radius > 0.f && std::isfinite(support_radius),
+                 "support_radius must be positive and finite");
+    DT_CHECK_ARG(n_triangles == 0 || n_vertices >= 1, "triangles need vertices");
+    if (n_points == 0) return DT_OK;
+    if (n_triangles > 0) {
+        REQUIRE_DEV(d_vertices, "d_vertices");
+        REQUIRE_DEV(d_triangles, "d_triangles");
+    }
+    REQUIRE_DEV(d_points, "d_points");
+    REQUIRE_DEV(d_normals, "d_normals");
+    REQUIRE_DEV(d_out, "d_out");
+    return launch_quicci(d_vertices, n_vertices, d_triangles, n_triangles, d_points, d_normals,
+                         n_points, support_radius, modified, d_out, (cudaStream_t)stream);
 }
 
 int dt_get_info(const dt_index *ix, dt_index_info *info)

@@ -75,6 +75,8 @@ def load():
         sig = {
             "dt_build": ([P, i64, P, P, P], ctypes.c_int),
             "dt_insert": ([P, P, i64, P], ctypes.c_int),
+            "quicci_generate": ([P, i64, P, i64, P, P, i64, ctypes.c_float, i32, P, P],
+                                ctypes.c_int),
             "dt_get_info": ([P, P], ctypes.c_int),
             "dt_export": ([P, P, P, P, P, P, P, P], ctypes.c_int),
             "dt_search": ([P, P, i64, i32, P, P, P, P, P], ctypes.c_int),
@@ -186,6 +188,30 @@ def dt_insert(index: Index, new, stream=None) -> Index:
     new = _desc(new, "new")
     _check(load().dt_insert(index.handle, _ptr(new), new.shape[0], _stream(stream)), "dt_insert")
     return index
+
+
+def quicci(vertices, triangles, points, normals, support_radius=100.0, modified=False,
+           out=None, stream=None):
+    """QUICCI (or modified QUICCI) descriptors of oriented points on a mesh.
+    vertices float32 [nv, 3], triangles int32 [nt, 3], points / normals
+    float32 [n, 3] (contiguous CUDA tensors); returns int64 [n, 64]."""
+    def f3(t, name, dtype):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.dim() == 2
+                and t.shape[1] == 3 and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous CUDA %s tensor of shape [n, 3]" % (name, dtype))
+        return t
+    vertices = f3(vertices, "vertices", torch.float32)
+    triangles = f3(triangles, "triangles", torch.int32)
+    points, normals = f3(points, "points", torch.float32), f3(normals, "normals", torch.float32)
+    if points.shape != normals.shape:
+        raise ValueError("points and normals must have the same shape")
+    if out is None:
+        out = torch.empty((points.shape[0], WORDS), dtype=torch.int64, device=points.device)
+    _check(load().quicci_generate(_ptr(vertices), vertices.shape[0], _ptr(triangles),
+                                  triangles.shape[0], _ptr(points), _ptr(normals), points.shape[0],
+                                  float(support_radius), 1 if modified else 0, _ptr(out),
+                                  _stream(stream)), "quicci_generate")
+    return out
 
 
 def _outputs(nq, k, device, with_ab, out):

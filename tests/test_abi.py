@@ -60,7 +60,7 @@ def test_bad_sizes_are_rejected():
 
 
 def test_new_entry_points_check_their_arguments_first():
-    """Warm-started search, inverted-file search, embedding and insertion reject bad
+    """Warm-started search, inverted-file search, embedding, insertion and QUICCI reject bad
     arguments with DT_EINVAL before touching the device."""
     from paper_2107_03368_gb300 import learned
     lib = learned._lib()
@@ -74,6 +74,10 @@ def test_new_entry_points_check_their_arguments_first():
     assert lib.ivf_search(None, None, None, 5, 1, 1, None, None, None, 0, None) == dt.DT_EINVAL
     assert lib.enc_embed(None, None, 5, None, None, 0, None) == dt.DT_EINVAL
     assert dt.load().dt_insert(None, None, 5, None) == dt.DT_EINVAL
+    assert dt.load().quicci_generate(None, 10, None, 5, None, None, 4, 0.0, 0, None,
+                                     None) == dt.DT_EINVAL
+    assert dt.load().quicci_generate(None, 0, None, 5, None, None, 4, 100.0, 0, None,
+                                     None) == dt.DT_EINVAL
 
 
 def test_tune_table_file_roundtrip(tmp_path):
