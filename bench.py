@@ -62,6 +62,10 @@ def parse_args(argv=None):
                    help="also sweep the encoder at its initial weights (1/0)")
     p.add_argument("--insert-n", type=int, default=100_000,
                    help="descriptors of new objects inserted into the tree (0: skip)")
+    p.add_argument("--quicci-objects", type=int, default=16,
+                   help="synthetic meshes for the QUICCI generation leg (0: skip)")
+    p.add_argument("--quicci-subdiv", type=int, default=5,
+                   help="mesh resolution: 5 = 10,242 vertices, 20,480 triangles")
     p.add_argument("--workload", choices=["tree", "tensor-bf"], default="tree",
                    help="tree: the tree-search step (default); tensor-bf: the large-batch "
                         "brute force, 65,536 queries x 20,000,000 descriptors")
@@ -424,6 +428,8 @@ def run_ours(a, dist):
     if not a.no_learned:
         line["learned"] = learned_leg(a, dist, d_db, d_q, db, value / dist.world, bf_best, stream,
                                       ix, tree_idx)
+    if a.quicci_objects > 0 and dist.rank == 0:
+        line["quicci"] = quicci_leg(a, dev, stream, nt)
     if a.insert_n > 0:                # last: it grows the index
         line["insert"] = insert_leg(a, ix, d_db, d_q, build_s, stream, nt)
 
@@ -452,6 +458,97 @@ def run_ours(a, dist):
         print(json.dumps(line), flush=True)
     ix.free()
     return 0
+
+
+def quicci_leg(a, dev, stream, nt):
+    """Descriptor generation from meshes (§2.2, §5) and the paper's pipeline
+    on its output: QUICCI of every vertex of complete synthetic objects,
+    modified QUICCI of every vertex of partial views (triangles facing a
+    random direction), a tree over the former, nearest neighbours and votes
+    of the latter; the partial views' original QUICCI for comparison."""
+    import torch
+    import oracle
+    from paper_2107_03368_gb300 import dt, synth
+
+    R = 100.0
+    n_obj = a.quicci_objects
+    meshes = [synth.mesh_object(SEED + 500 + o, a.quicci_subdiv) for o in range(n_obj)]
+    parts = [synth.mesh_partial(SEED + 900 + o, m[0], m[1])[:3] for o, m in enumerate(meshes)]
+    f32 = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).to(dev)
+    i32 = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.int32)).to(dev)
+    d_full = [(f32(v), i32(t), f32(n)) for v, t, n in meshes]
+    d_part = [(f32(v), i32(t), f32(n)) for v, t, n in parts]
+
+    def run(dm, modified):
+        outs = [torch.empty((v.shape[0], 64), dtype=torch.int64, device=dev) for v, _, _ in dm]
+        dt.quicci(dm[0][0], dm[0][1], dm[0][0], dm[0][2], R, modified, out=outs[0])   # warm
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        with nvtx("quicci_%s" % ("modified" if modified else "full")):
+            for (v, t, n), o in zip(dm, outs):
+                dt.quicci(v, t, v, n, R, modified, out=o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return outs, e0.elapsed_time(e1) / 1e3, time.perf_counter() - t0
+
+    full, s_full, w_full = run(d_full, False)
+    part, s_part, w_part = run(d_part, True)
+    part_orig, _, _ = run(d_part, False)
+    n_full = sum(v.shape[0] for v, _, _ in meshes)
+    pairs_full = sum(v.shape[0] * t.shape[0] for v, t, _ in meshes)
+    n_part = sum(v.shape[0] for v, _, _ in parts)
+
+    db = torch.cat(full)
+    obj = torch.cat([torch.full((v.shape[0],), o, dtype=torch.int32, device=dev)
+                     for o, (v, _, _) in enumerate(meshes)])
+    off = torch.tensor(np.concatenate([[0], np.cumsum([v.shape[0] for v, _, _ in parts])]),
+                       dtype=torch.int64, device=dev)
+    ix = dt.dt_build(db)
+    truth = torch.arange(n_obj, dtype=torch.int32, device=dev)
+    src = torch.cat([torch.full((v.shape[0],), o, dtype=torch.int32, device=dev)
+                     for o, (v, _, _) in enumerate(parts)])
+    pipeline = {}
+    for name, q in (("modified", part), ("original", part_orig)):
+        qd = torch.cat(q)
+        _, winner, _ = dt.retrieve_objects(ix, obj, n_obj, qd, off, 0, 1)
+        nn, _, _ = dt.bf_search(db, qd, 1, path=2)
+        nn_obj = obj[nn[:, 0].long()]
+        pipeline[name] = {"objects_identified": int((winner == truth).sum()),
+                          "nn_from_source_object": float((nn_obj == src).float().mean())}
+    ix.free()
+
+    # the oracle on a bounded sample: 48 vertices of the first object
+    v0, t0_, n0 = meshes[0]
+    pick = np.linspace(0, v0.shape[0] - 1, 48).astype(np.int64)
+    c0 = time.perf_counter()
+    ref = oracle.quicci(v0, t0_, v0[pick], n0[pick], R, False, nthreads=nt)
+    cpu_s = time.perf_counter() - c0
+    same = int((full[0][pick].cpu().numpy().view(np.uint64) == ref).all(axis=1).sum())
+
+    # cull-step roofline: rejecting a (point, triangle) pair takes at least
+    # 13 FP32 operations (offset 3, height 3, side test 1, radial offset 3,
+    # squared norm 3) plus one square root; 152 SMs x 128 FP32 lanes x clock
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    pk = peaks()
+    pair_peak = sms * 128 * pk["sm_max_mhz"] * 1e6 / 13.0
+    return {"objects": n_obj, "vertices_per_object": int(meshes[0][0].shape[0]),
+            "triangles_per_object": int(meshes[0][1].shape[0]), "support_radius": R,
+            "complete": {"descriptors": n_full, "seconds": s_full, "wall_s": w_full,
+                         "descriptors_per_s": n_full / s_full,
+                         "point_triangle_pairs_per_s": pairs_full / s_full},
+            "partial_modified": {"descriptors": n_part, "seconds": s_part, "wall_s": w_part,
+                                 "descriptors_per_s": n_part / s_part},
+            "roofline": {"bound": "alu", "achieved": pairs_full / s_full / 1e12,
+                         "peak": pair_peak / 1e12, "unit": "Tpairs/s",
+                         "frac": pairs_full / s_full / pair_peak,
+                         "peak_kind": "%d SMs x 128 FP32 lanes x %.0f MHz / 13 FP32 ops per "
+                                      "rejected pair" % (sms, pk["sm_max_mhz"])},
+            "pipeline": pipeline,
+            "cpu_baseline": {"value": 48 / cpu_s, "unit": "descriptors/s", "cores": nt,
+                             "kind": "oracle", "sample": "48 vertices of the first object",
+                             "identical_descriptors": same}}
 
 
 def insert_leg(a, ix, d_db, d_q, build_s, stream, nt):

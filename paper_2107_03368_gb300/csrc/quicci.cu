@@ -15,9 +15,10 @@
 // the segment once on each side of that point with dm < r <= that side's end
 // distance.  So a segment changes the count of circle c by +1 at the first
 // circle beyond dm and by -1 at the first circle beyond each end distance:
-// the first circle with radius > x is c(x) = floor(x * 64 / R).  A warp owns
-// one point and accumulates these signed changes, per (layer, circle), in
-// shared memory; the bit is then just "change != 0" (or |change| >= 2).
+// the first circle with radius > x is c(x) = floor(x * 64 / R).
+// A CTA owns one point and accumulates these signed changes, per (layer,
+// circle), in shared memory; the bit is then just "change != 0" (or
+// |change| >= 2).
 //
 // Work: every triangle is tested against every point (cheap rejection by the
 // triangle's bounding sphere against the support cylinder); triangles are
@@ -32,8 +33,10 @@ namespace dtk {
 namespace {
 
 constexpr int QN = 64;            // layers, circles per layer
-constexpr int kQWarps = 4;        // points per CTA, one per warp
-constexpr size_t kQSmem = (size_t)kQWarps * QN * QN * sizeof(int);
+constexpr int kQThreads = 128;    // threads per CTA, one CTA per point
+constexpr int kQWarps = kQThreads / 32;
+constexpr int kQBlocksPerSm = 8;  // 64 registers per thread
+constexpr size_t kQSmem = (size_t)QN * QN * sizeof(int);
 
 struct PackedTri {
     float4 v0, v1, v2;            // xyz, w unused
@@ -86,6 +89,13 @@ __device__ __forceinline__ float3 axpy3(float s, float3 x, float3 y)
     return make_float3(fmaf(s, x.x, y.x), fmaf(s, x.y, y.y), fmaf(s, x.z, y.z));
 }
 
+// One of three values by index, without indexing an array (which would
+// place the array in local memory).
+template <class T> __device__ __forceinline__ T pick3(int i, T a, T b, T c)
+{
+    return i == 0 ? a : (i == 1 ? b : c);
+}
+
 // First circle with radius > x (QN: none).
 __device__ __forceinline__ int circle_after(float x, float inv_step)
 {
@@ -103,27 +113,28 @@ __device__ __forceinline__ void add_branch(int *row, float dm, float end, float 
     if (c1 < QN) atomicAdd(&row[c1], -1);
 }
 
-__global__ void __launch_bounds__(kQWarps * 32)
+// One CTA per oriented point (persistent over points): its threads take the
+// triangles in turn and add their segments' count changes to the point's
+// 64 x 64 counters in shared memory; the four warps then turn 16 layers each
+// into descriptor words.
+__global__ void __launch_bounds__(kQThreads, kQBlocksPerSm)
 quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float *__restrict__ points,
               const float *__restrict__ normals, int64_t np, float R, int modified,
               uint64_t *__restrict__ out)
 {
-    extern __shared__ __align__(16) int q_smem[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int *cnt = q_smem + (size_t)w * QN * QN;
+    extern __shared__ __align__(16) int cnt[];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const float step = R / QN, inv_step = QN / R;
     const float R2 = R * R;
-    int64_t j = (int64_t)blockIdx.x * kQWarps + w;
-    const int64_t nwarps = (int64_t)gridDim.x * kQWarps;
-    for (; j < np; j += nwarps) {
-        for (int i = lane; i < QN * QN / 4; i += 32) reinterpret_cast<int4 *>(cnt)[i] = make_int4(0, 0, 0, 0);
-        __syncwarp();
+    for (int64_t j = blockIdx.x; j < np; j += gridDim.x) {
+        for (int i = tid; i < QN * QN / 4; i += kQThreads) reinterpret_cast<int4 *>(cnt)[i] = make_int4(0, 0, 0, 0);
+        __syncthreads();
         const float3 p = make_float3(points[j * 3], points[j * 3 + 1], points[j * 3 + 2]);
         float3 n = make_float3(normals[j * 3], normals[j * 3 + 1], normals[j * 3 + 2]);
         const float len = sqrtf(dot3(n, n));
         if (len > 0.f) {
             n = make_float3(n.x / len, n.y / len, n.z / len);
-            for (int64_t t = lane; t < nt; t += 32) {
+            for (int64_t t = tid; t < nt; t += kQThreads) {
                 const float4 sp = __ldg(&tris[t].sphere);
                 if (sp.w < 0.f) continue;
                 const float3 rc = sub3(make_float3(sp.x, sp.y, sp.z), p);
@@ -155,25 +166,22 @@ quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float *__res
                     const bool b0 = z[0] < zl, b1 = z[1] < zl, b2 = z[2] < zl;
                     const int nb = (int)b0 + (int)b1 + (int)b2;
                     if (nb == 0 || nb == 3) continue;
-                    // the two crossing edges, in edge order (0,1), (1,2), (2,0)
-                    float3 e[2];
-                    int ne = 0;
-                    const bool bs[3] = {b0, b1, b2};
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const int a = k, b = (k + 1) % 3;
-                        if (bs[a] == bs[b]) continue;
-                        const float s = (zl - z[a]) / (z[b] - z[a]);
-                        const float3 pt = axpy3(s, sub3(q[b], q[a]), q[a]);
-                        if (ne < 2) e[ne] = pt;
-                        ++ne;
-                    }
-                    const float3 d = sub3(e[1], e[0]);
+                    // the two crossing edges, in edge order (0,1), (1,2), (2,0);
+                    // the vertex alone on its side starts both of them
+                    const int solo = (b0 != b1) ? ((b0 != b2) ? 0 : 1) : 2;
+                    const int o1 = solo == 2 ? 0 : solo + 1, o2 = solo == 0 ? 2 : solo - 1;
+                    const float zs = pick3(solo, z[0], z[1], z[2]);
+                    const float3 qs = pick3(solo, q[0], q[1], q[2]);
+                    const float s1 = (zl - zs) / (pick3(o1, z[0], z[1], z[2]) - zs);
+                    const float s2 = (zl - zs) / (pick3(o2, z[0], z[1], z[2]) - zs);
+                    const float3 e0 = axpy3(s1, sub3(pick3(o1, q[0], q[1], q[2]), qs), qs);
+                    const float3 e1 = axpy3(s2, sub3(pick3(o2, q[0], q[1], q[2]), qs), qs);
+                    const float3 d = sub3(e1, e0);
                     const float dd = dot3(d, d);
-                    const float d0 = sqrtf(dot3(e[0], e[0])), d1 = sqrtf(dot3(e[1], e[1]));
-                    float ts = dd > 0.f ? -dot3(e[0], d) / dd : 0.f;
+                    const float d0 = sqrtf(dot3(e0, e0)), d1 = sqrtf(dot3(e1, e1));
+                    float ts = dd > 0.f ? -dot3(e0, d) / dd : 0.f;
                     ts = fminf(fmaxf(ts, 0.f), 1.f);
-                    const float3 cp = axpy3(ts, d, e[0]);
+                    const float3 cp = axpy3(ts, d, e0);
                     const float dm = fminf(sqrtf(dot3(cp, cp)), fminf(d0, d1));
                     int *row = cnt + l * QN;
                     add_branch(row, dm, d0, inv_step);
@@ -181,18 +189,16 @@ quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float *__res
                 }
             }
         }
-        __syncwarp();
-        // one layer per step: lanes hold circles lane and lane + 32
-        uint64_t mine = 0;
-        for (int l = 0; l < QN; ++l) {
+        __syncthreads();
+        // warp w: layers 16w .. 16w + 15, lanes hold circles lane and lane + 32
+        for (int l = w * (QN / kQWarps); l < (w + 1) * (QN / kQWarps); ++l) {
             const int v0 = cnt[l * QN + lane], v1 = cnt[l * QN + 32 + lane];
             const bool s0 = modified ? (v0 >= 2 || v0 <= -2) : v0 != 0;
             const bool s1 = modified ? (v1 >= 2 || v1 <= -2) : v1 != 0;
             const uint32_t lo = __ballot_sync(0xffffffffu, s0), hi = __ballot_sync(0xffffffffu, s1);
-            if (lane == (l & 31)) mine = ((uint64_t)hi << 32) | lo;
-            if ((l & 31) == 31) out[j * QN + (l - 31) + lane] = mine;
+            if (lane == 0) out[j * QN + l] = ((uint64_t)hi << 32) | lo;
         }
-        __syncwarp();
+        __syncthreads();
     }
 }
 
@@ -222,8 +228,8 @@ int launch_quicci(const float *d_vertices, int64_t n_vertices, const int32_t *d_
     DT_CUDA_TRY(cudaStreamSynchronize(s));
     DT_CHECK_ARG(!h_bad, "a triangle vertex id is outside [0, n_vertices)");
     DT_CUDA_TRY(allow_smem((const void *)quicci_kernel, (int)kQSmem));
-    const int64_t blocks = std::min<int64_t>((n_points + kQWarps - 1) / kQWarps, (int64_t)sm_count() * 16);
-    quicci_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), kQWarps * 32, kQSmem, s>>>(
+    const int64_t blocks = std::min<int64_t>(n_points, (int64_t)sm_count() * kQBlocksPerSm);
+    quicci_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), kQThreads, kQSmem, s>>>(
         packed, n_triangles, d_points, d_normals, n_points, support_radius, modified ? 1 : 0, d_out);
     DT_CUDA_TRY(cudaGetLastError());
     // the packed triangles are freed on the stream after the kernel
