@@ -28,13 +28,12 @@
 #include <algorithm>
 #include <vector>
 
-#include "block_util.cuh"
 #include "dt_internal.cuh"
+#include "sort_util.cuh"
 
 namespace dtk {
 namespace {
 
-constexpr int kSortTile = 4096;   // keys per warp in the radix passes
 constexpr int kRun = 64;          // rows per warp in the shift
 constexpr int kSegChunk = 4096;   // rows per block when permuting rebuilt segments
 
@@ -136,70 +135,6 @@ widen_kernel(const uint64_t *__restrict__ d_new, int64_t m, const NodeRec *__res
             const NodeRec rs = node[s];
             at = target < rs.begin + rs.count ? s : s + 1;
         }
-    }
-}
-
-// 2. Stable LSD radix sort of (key, val) pairs, 8 bits per pass.  A warp owns
-// a tile of kSortTile consecutive pairs; the per-(digit, tile) counts are
-// scanned digit-major, so equal digits keep tile order, and inside a tile
-// equal digits keep lane order within each 32-pair step.
-__global__ void __launch_bounds__(128)
-radix_hist_kernel(const uint32_t *__restrict__ keys, int64_t m, int shift, int64_t n_tiles,
-                  uint32_t *__restrict__ hist)
-{
-    __shared__ uint32_t h[4][256];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = lane; i < 256; i += 32) h[w][i] = 0;
-    __syncwarp();
-    const int64_t tile = (int64_t)blockIdx.x * 4 + w;
-    if (tile >= n_tiles) return;
-    const int64_t b = tile * kSortTile, e = std::min<int64_t>(b + kSortTile, m);
-    for (int64_t i = b + lane; i < e; i += 32) atomicAdd(&h[w][(keys[i] >> shift) & 255u], 1u);
-    __syncwarp();
-    for (int d = lane; d < 256; d += 32) hist[(int64_t)d * n_tiles + tile] = h[w][d];
-}
-
-__global__ void __launch_bounds__(1024) excl_scan_kernel(uint32_t *a, int64_t len)
-{
-    __shared__ uint32_t tmp[33];
-    uint32_t run = 0;
-    for (int64_t c0 = 0; c0 < len; c0 += blockDim.x) {
-        const int64_t c = c0 + threadIdx.x;
-        uint32_t tot;
-        const uint32_t before = block_excl_scan(c < len ? a[c] : 0u, tmp, &tot);
-        if (c < len) a[c] = run + before;
-        run += tot;
-    }
-}
-
-__global__ void __launch_bounds__(128)
-radix_scatter_kernel(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, int64_t m,
-                     int shift, int64_t n_tiles, const uint32_t *__restrict__ hist,
-                     uint32_t *__restrict__ kout, uint32_t *__restrict__ vout)
-{
-    __shared__ uint32_t base[4][256];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t tile = (int64_t)blockIdx.x * 4 + w;
-    if (tile >= n_tiles) return;
-    for (int d = lane; d < 256; d += 32) base[w][d] = hist[(int64_t)d * n_tiles + tile];
-    __syncwarp();
-    const int64_t b = tile * kSortTile, e = std::min<int64_t>(b + kSortTile, m);
-    const unsigned below = (1u << lane) - 1u;
-    for (int64_t c = b; c < e; c += 32) {
-        const int64_t i = c + lane;
-        const bool valid = i < e;
-        const uint32_t k = valid ? kin[i] : 0u;
-        const uint32_t dg = valid ? ((k >> shift) & 255u) : 256u + (uint32_t)lane;   // unique if invalid
-        const unsigned peers = __match_any_sync(0xffffffffu, dg);
-        const uint32_t rank = (uint32_t)__popc(peers & below);
-        if (valid) {
-            const uint32_t pos = base[w][dg] + rank;
-            kout[pos] = k;
-            vout[pos] = vin[i];
-        }
-        __syncwarp();
-        if (valid && rank == 0) base[w][dg] += (uint32_t)__popc(peers);
-        __syncwarp();
     }
 }
 
@@ -340,7 +275,7 @@ int insert_tree(dt_index *ix, const uint64_t *d_new, int64_t m, cudaStream_t s)
              *hist = nullptr;
     int *err = nullptr;
     NodeRec *node_tmp = nullptr;
-    const int64_t n_tiles = (m + kSortTile - 1) / kSortTile;
+    const int64_t n_tiles = radix_tiles(m);
     DT_CUDA_TRY(scratch.alloc(&leaf_of, (size_t)m * 4));
     DT_CUDA_TRY(scratch.alloc(&keys, (size_t)m * 4));
     DT_CUDA_TRY(scratch.alloc(&vals, (size_t)m * 4));
@@ -379,15 +314,7 @@ int insert_tree(dt_index *ix, const uint64_t *d_new, int64_t m, cudaStream_t s)
     // 2. stable sort by leaf end (keys <= n_old)
     int bits = 1;
     while (bits < 32 && (n_old >> bits) != 0) ++bits;
-    for (int shift = 0; shift < bits; shift += 8) {
-        const unsigned blocks = (unsigned)((n_tiles + 3) / 4);
-        radix_hist_kernel<<<blocks, 128, 0, s>>>(keys, m, shift, n_tiles, hist);
-        excl_scan_kernel<<<1, 1024, 0, s>>>(hist, n_tiles * 256);
-        radix_scatter_kernel<<<blocks, 128, 0, s>>>(keys, vals, m, shift, n_tiles, hist, keys2, vals2);
-        DT_CUDA_TRY(cudaGetLastError());
-        std::swap(keys, keys2);
-        std::swap(vals, vals2);
-    }
+    DT_CUDA_TRY(radix_sort_pairs(&keys, &vals, &keys2, &vals2, m, bits, hist, s));
 
     // 4. shifted rows and segments
     Owned db_new, perm_new, iperm_new, node_new, or_new, and_new;

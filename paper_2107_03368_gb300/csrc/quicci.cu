@@ -20,14 +20,20 @@
 // circle), in shared memory; the bit is then just "change != 0" (or
 // |change| >= 2).
 //
-// Work: every triangle is tested against every point (cheap rejection by the
-// triangle's bounding sphere against the support cylinder); triangles are
-// pre-packed as three vertices plus a bounding sphere, 64 bytes, and read
-// through the read-only cache by all warps.  Arithmetic is FP32.
+// Work: every triangle is tested against every point, in two levels.  The
+// triangles are packed (three vertices and a bounding sphere, 64 bytes) and
+// sorted along a Morton curve of their centroids, so that each run of 32
+// consecutive triangles (a group) is a compact patch with a bounding sphere
+// of its own; a warp rejects a whole group against the point's support
+// cylinder with one test, and only the groups that pass are tested triangle
+// by triangle, one per lane.  Counts are integer sums, so the order in which
+// triangles are visited changes nothing.  Arithmetic is FP32.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "dt_internal.cuh"
+#include "sort_util.cuh"
 
 namespace dtk {
 namespace {
@@ -37,6 +43,7 @@ constexpr int kQThreads = 128;    // threads per CTA, one CTA per point
 constexpr int kQWarps = kQThreads / 32;
 constexpr int kQBlocksPerSm = 8;  // 64 registers per thread
 constexpr size_t kQSmem = (size_t)QN * QN * sizeof(int);
+constexpr int kGroup = 32;        // triangles per group (one per lane)
 
 struct PackedTri {
     float4 v0, v1, v2;            // xyz, w unused
@@ -82,6 +89,124 @@ __global__ void pack_triangles_kernel(const float *__restrict__ vertices, int64_
     }
 }
 
+// Order-preserving map of a float to a signed int (for atomic min / max).
+__device__ __forceinline__ int ordered(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// Bounding box of the triangle centres: box[0..2] min, box[3..5] max, as
+// ordered ints (box initialised to +max / -max by the host).
+__global__ void centre_box_kernel(const PackedTri *__restrict__ tris, int64_t nt, int *__restrict__ box)
+{
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; t < nt; t += stride) {
+        const float4 c = tris[t].sphere;
+        const int o[3] = {ordered(c.x), ordered(c.y), ordered(c.z)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = min(lo[k], o[k]);
+            hi[k] = max(hi[k], o[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], d));
+            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], d));
+        }
+    }
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&box[k], lo[k]);
+            atomicMax(&box[3 + k], hi[k]);
+        }
+}
+
+// Spreads the low 10 bits of x to every third bit (bit i -> bit 3i).
+__device__ __forceinline__ uint32_t spread3(uint32_t x)
+{
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+// Morton key (10 bits per axis) of each triangle centre within the box.
+__global__ void morton_kernel(const PackedTri *__restrict__ tris, int64_t nt, const int *__restrict__ box,
+                              uint32_t *__restrict__ key, uint32_t *__restrict__ val)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    float lo[3], scale[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = unordered(box[k]);
+        const float ext = unordered(box[3 + k]) - lo[k];
+        scale[k] = ext > 0.f ? 1023.f / ext : 0.f;
+    }
+    for (; t < nt; t += stride) {
+        const float4 c = tris[t].sphere;
+        const float cc[3] = {c.x, c.y, c.z};
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float f = fminf(fmaxf((cc[k] - lo[k]) * scale[k], 0.f), 1023.f);
+            m |= spread3((uint32_t)f) << k;
+        }
+        key[t] = m;
+        val[t] = (uint32_t)t;
+    }
+}
+
+__global__ void gather_tris_kernel(const PackedTri *__restrict__ in, const uint32_t *__restrict__ order,
+                                   int64_t nt, PackedTri *__restrict__ out)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; t < nt; t += stride) out[t] = in[order[t]];
+}
+
+// A warp per group of kGroup consecutive triangles: a sphere holding all of
+// their spheres (centre: mean of their centres).
+__global__ void group_sphere_kernel(const PackedTri *__restrict__ tris, int64_t nt, int64_t n_groups,
+                                    float4 *__restrict__ groups)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (; g < n_groups; g += nw) {
+        const int64_t t = g * kGroup + lane;
+        const bool have = t < nt;
+        const float4 c = have ? tris[t].sphere : make_float4(0.f, 0.f, 0.f, 0.f);
+        float sx = c.x, sy = c.y, sz = c.z, cntf = have ? 1.f : 0.f;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, d);
+            sy += __shfl_xor_sync(0xffffffffu, sy, d);
+            sz += __shfl_xor_sync(0xffffffffu, sz, d);
+            cntf += __shfl_xor_sync(0xffffffffu, cntf, d);
+        }
+        const float cx = sx / cntf, cy = sy / cntf, cz = sz / cntf;
+        float r = 0.f;
+        if (have) {
+            const float dx = c.x - cx, dy = c.y - cy, dz = c.z - cz;
+            r = sqrtf(dx * dx + dy * dy + dz * dz) + c.w;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, d));
+        // widened like the triangles' spheres, so rounding never rejects a
+        // group that reaches the support cylinder
+        if (lane == 0) groups[g] = make_float4(cx, cy, cz, r * 1.0001f + 1e-3f);
+    }
+}
+
 __device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 __device__ __forceinline__ float3 axpy3(float s, float3 x, float3 y)
@@ -113,14 +238,80 @@ __device__ __forceinline__ void add_branch(int *row, float dm, float end, float 
     if (c1 < QN) atomicAdd(&row[c1], -1);
 }
 
-// One CTA per oriented point (persistent over points): its threads take the
-// triangles in turn and add their segments' count changes to the point's
-// 64 x 64 counters in shared memory; the four warps then turn 16 layers each
-// into descriptor words.
+// Whether a sphere (centre xyz, radius w) reaches the support cylinder of the
+// point p with unit axis n: |height| <= R + radius and distance from the
+// axis <= R + radius.
+__device__ __forceinline__ bool reaches(float4 sp, float3 p, float3 n, float R, float R2)
+{
+    const float3 rc = sub3(make_float3(sp.x, sp.y, sp.z), p);
+    const float zc = dot3(rc, n);
+    if (fabsf(zc) - sp.w > R) return false;
+    const float3 qc = axpy3(-zc, n, rc);
+    const float rad = sqrtf(dot3(qc, qc)) - sp.w;
+    return !(rad > 0.f && rad * rad > R2);
+}
+
+// Adds the count changes of triangle t's layer segments to the counters.
+__device__ __forceinline__ void add_triangle(const PackedTri *__restrict__ tris, int64_t t, float3 p,
+                                             float3 n, float R, float R2, float step, float inv_step,
+                                             int *cnt)
+{
+    if (!reaches(__ldg(&tris[t].sphere), p, n, R, R2)) return;
+    const float4 a4 = __ldg(&tris[t].v0), b4 = __ldg(&tris[t].v1), c4 = __ldg(&tris[t].v2);
+    float z[3];
+    float3 q[3];
+    const float3 rel[3] = {sub3(make_float3(a4.x, a4.y, a4.z), p), sub3(make_float3(b4.x, b4.y, b4.z), p),
+                           sub3(make_float3(c4.x, c4.y, c4.z), p)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        z[i] = dot3(rel[i], n);
+        q[i] = axpy3(-z[i], n, rel[i]);
+    }
+    const float zmin = fminf(z[0], fminf(z[1], z[2])), zmax = fmaxf(z[0], fmaxf(z[1], z[2]));
+    // layers with z_l in (zmin, zmax], widened by one on each side; the exact
+    // side test below decides
+    int l0 = (int)floorf((zmin + R) * (0.5f * inv_step) - 0.5f);
+    int l1 = (int)ceilf((zmax + R) * (0.5f * inv_step) - 0.5f);
+    l0 = max(l0, 0);
+    l1 = min(l1, QN - 1);
+    for (int l = l0; l <= l1; ++l) {
+        const float zl = -R + (2.f * l + 1.f) * step;
+        const bool b0 = z[0] < zl, b1 = z[1] < zl, b2 = z[2] < zl;
+        const int nb = (int)b0 + (int)b1 + (int)b2;
+        if (nb == 0 || nb == 3) continue;
+        // the two crossing edges both start at the vertex alone on its side
+        const int solo = (b0 != b1) ? ((b0 != b2) ? 0 : 1) : 2;
+        const int o1 = solo == 2 ? 0 : solo + 1, o2 = solo == 0 ? 2 : solo - 1;
+        const float zs = pick3(solo, z[0], z[1], z[2]);
+        const float3 qs = pick3(solo, q[0], q[1], q[2]);
+        const float s1 = (zl - zs) / (pick3(o1, z[0], z[1], z[2]) - zs);
+        const float s2 = (zl - zs) / (pick3(o2, z[0], z[1], z[2]) - zs);
+        const float3 e0 = axpy3(s1, sub3(pick3(o1, q[0], q[1], q[2]), qs), qs);
+        const float3 e1 = axpy3(s2, sub3(pick3(o2, q[0], q[1], q[2]), qs), qs);
+        const float3 d = sub3(e1, e0);
+        const float dd = dot3(d, d);
+        const float d0 = sqrtf(dot3(e0, e0)), d1 = sqrtf(dot3(e1, e1));
+        float ts = dd > 0.f ? -dot3(e0, d) / dd : 0.f;
+        ts = fminf(fmaxf(ts, 0.f), 1.f);
+        const float3 cp = axpy3(ts, d, e0);
+        const float dm = fminf(sqrtf(dot3(cp, cp)), fminf(d0, d1));
+        int *row = cnt + l * QN;
+        add_branch(row, dm, d0, inv_step);
+        add_branch(row, dm, d1, inv_step);
+    }
+}
+
+// One CTA per oriented point (persistent over points).  Each warp takes 32
+// triangle groups at a time, one per lane (interleaved with the other
+// warps' groups), and tests them against the
+// support cylinder; then, for every group that passed (a warp-wide ballot),
+// its lanes take the group's triangles, one each, and add their segments'
+// count changes to the point's 64 x 64 counters in shared memory.  The four
+// warps then turn 16 layers each into descriptor words.
 __global__ void __launch_bounds__(kQThreads, kQBlocksPerSm)
-quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float *__restrict__ points,
-              const float *__restrict__ normals, int64_t np, float R, int modified,
-              uint64_t *__restrict__ out)
+quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float4 *__restrict__ groups,
+              int64_t n_groups, const float *__restrict__ points, const float *__restrict__ normals,
+              int64_t np, float R, int modified, uint64_t *__restrict__ out)
 {
     extern __shared__ __align__(16) int cnt[];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -134,58 +325,17 @@ quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float *__res
         const float len = sqrtf(dot3(n, n));
         if (len > 0.f) {
             n = make_float3(n.x / len, n.y / len, n.z / len);
-            for (int64_t t = tid; t < nt; t += kQThreads) {
-                const float4 sp = __ldg(&tris[t].sphere);
-                if (sp.w < 0.f) continue;
-                const float3 rc = sub3(make_float3(sp.x, sp.y, sp.z), p);
-                const float zc = dot3(rc, n);
-                if (fabsf(zc) - sp.w > R) continue;
-                const float3 qc = axpy3(-zc, n, rc);
-                const float rad = sqrtf(dot3(qc, qc)) - sp.w;
-                if (rad > 0.f && rad * rad > R2) continue;
-                const float4 a4 = __ldg(&tris[t].v0), b4 = __ldg(&tris[t].v1), c4 = __ldg(&tris[t].v2);
-                float z[3];
-                float3 q[3];
-                const float3 rel[3] = {sub3(make_float3(a4.x, a4.y, a4.z), p),
-                                       sub3(make_float3(b4.x, b4.y, b4.z), p),
-                                       sub3(make_float3(c4.x, c4.y, c4.z), p)};
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    z[i] = dot3(rel[i], n);
-                    q[i] = axpy3(-z[i], n, rel[i]);
-                }
-                const float zmin = fminf(z[0], fminf(z[1], z[2])), zmax = fmaxf(z[0], fmaxf(z[1], z[2]));
-                // layers with z_l in (zmin, zmax], widened by one on each side;
-                // the exact side test below decides
-                int l0 = (int)floorf((zmin + R) * (0.5f * inv_step) - 0.5f);
-                int l1 = (int)ceilf((zmax + R) * (0.5f * inv_step) - 0.5f);
-                l0 = max(l0, 0);
-                l1 = min(l1, QN - 1);
-                for (int l = l0; l <= l1; ++l) {
-                    const float zl = -R + (2.f * l + 1.f) * step;
-                    const bool b0 = z[0] < zl, b1 = z[1] < zl, b2 = z[2] < zl;
-                    const int nb = (int)b0 + (int)b1 + (int)b2;
-                    if (nb == 0 || nb == 3) continue;
-                    // the two crossing edges, in edge order (0,1), (1,2), (2,0);
-                    // the vertex alone on its side starts both of them
-                    const int solo = (b0 != b1) ? ((b0 != b2) ? 0 : 1) : 2;
-                    const int o1 = solo == 2 ? 0 : solo + 1, o2 = solo == 0 ? 2 : solo - 1;
-                    const float zs = pick3(solo, z[0], z[1], z[2]);
-                    const float3 qs = pick3(solo, q[0], q[1], q[2]);
-                    const float s1 = (zl - zs) / (pick3(o1, z[0], z[1], z[2]) - zs);
-                    const float s2 = (zl - zs) / (pick3(o2, z[0], z[1], z[2]) - zs);
-                    const float3 e0 = axpy3(s1, sub3(pick3(o1, q[0], q[1], q[2]), qs), qs);
-                    const float3 e1 = axpy3(s2, sub3(pick3(o2, q[0], q[1], q[2]), qs), qs);
-                    const float3 d = sub3(e1, e0);
-                    const float dd = dot3(d, d);
-                    const float d0 = sqrtf(dot3(e0, e0)), d1 = sqrtf(dot3(e1, e1));
-                    float ts = dd > 0.f ? -dot3(e0, d) / dd : 0.f;
-                    ts = fminf(fmaxf(ts, 0.f), 1.f);
-                    const float3 cp = axpy3(ts, d, e0);
-                    const float dm = fminf(sqrtf(dot3(cp, cp)), fminf(d0, d1));
-                    int *row = cnt + l * QN;
-                    add_branch(row, dm, d0, inv_step);
-                    add_branch(row, dm, d1, inv_step);
+            // lane i of warp w tests group g0 + i * kQWarps + w: neighbouring
+            // groups (often reached together) go to different warps
+            for (int64_t g0 = 0; g0 < n_groups; g0 += (int64_t)kQWarps * 32) {
+                const int64_t g = g0 + (int64_t)lane * kQWarps + w;
+                const bool hit = g < n_groups && reaches(__ldg(&groups[g]), p, n, R, R2);
+                uint32_t mask = __ballot_sync(0xffffffffu, hit);
+                while (mask) {
+                    const int b = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int64_t t = (g0 + (int64_t)b * kQWarps + w) * kGroup + lane;
+                    if (t < nt) add_triangle(tris, t, p, n, R, R2, step, inv_step, cnt);
                 }
             }
         }
@@ -227,10 +377,41 @@ int launch_quicci(const float *d_vertices, int64_t n_vertices, const int32_t *d_
     DT_CUDA_TRY(cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     DT_CUDA_TRY(cudaStreamSynchronize(s));
     DT_CHECK_ARG(!h_bad, "a triangle vertex id is outside [0, n_vertices)");
+    // spatial order: Morton keys of the centres, stable radix sort, gather
+    const int64_t n_groups = (n_triangles + kGroup - 1) / kGroup;
+    PackedTri *sorted = nullptr;
+    float4 *groups = nullptr;
+    uint32_t *key = nullptr, *val = nullptr, *key2 = nullptr, *val2 = nullptr, *hist = nullptr;
+    int *box = nullptr;
+    if (n_triangles > 0) {
+        const int64_t nt = n_triangles;
+        DT_CUDA_TRY(scratch.alloc(&sorted, (size_t)nt * sizeof(PackedTri)));
+        DT_CUDA_TRY(scratch.alloc(&groups, (size_t)n_groups * sizeof(float4)));
+        DT_CUDA_TRY(scratch.alloc(&key, (size_t)nt * 4));
+        DT_CUDA_TRY(scratch.alloc(&val, (size_t)nt * 4));
+        DT_CUDA_TRY(scratch.alloc(&key2, (size_t)nt * 4));
+        DT_CUDA_TRY(scratch.alloc(&val2, (size_t)nt * 4));
+        DT_CUDA_TRY(scratch.alloc(&hist, (size_t)radix_tiles(nt) * 256 * 4));
+        DT_CUDA_TRY(scratch.alloc(&box, 6 * sizeof(int)));
+        const int h_box[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
+        DT_CUDA_TRY(cudaMemcpyAsync(box, h_box, sizeof(h_box), cudaMemcpyHostToDevice, s));
+        const unsigned gb = (unsigned)std::min<int64_t>((nt + 255) / 256, 4096);
+        centre_box_kernel<<<gb, 256, 0, s>>>(packed, nt, box);
+        morton_kernel<<<gb, 256, 0, s>>>(packed, nt, box, key, val);
+        DT_CUDA_TRY(cudaGetLastError());
+        DT_CUDA_TRY(radix_sort_pairs(&key, &val, &key2, &val2, nt, 30, hist, s));
+        gather_tris_kernel<<<gb, 256, 0, s>>>(packed, val, nt, sorted);
+        group_sphere_kernel<<<(unsigned)std::min<int64_t>((n_groups + 7) / 8, 8192), 256, 0, s>>>(
+            sorted, nt, n_groups, groups);
+        DT_CUDA_TRY(cudaGetLastError());
+        // h_box must outlive its upload
+        DT_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     DT_CUDA_TRY(allow_smem((const void *)quicci_kernel, (int)kQSmem));
     const int64_t blocks = std::min<int64_t>(n_points, (int64_t)sm_count() * kQBlocksPerSm);
     quicci_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), kQThreads, kQSmem, s>>>(
-        packed, n_triangles, d_points, d_normals, n_points, support_radius, modified ? 1 : 0, d_out);
+        sorted, n_triangles, groups, n_groups, d_points, d_normals, n_points, support_radius,
+        modified ? 1 : 0, d_out);
     DT_CUDA_TRY(cudaGetLastError());
     // the packed triangles are freed on the stream after the kernel
     return DT_OK;
