@@ -42,7 +42,8 @@ constexpr int QN = 64;            // layers, circles per layer
 constexpr int kQThreads = 128;    // threads per CTA, one CTA per point
 constexpr int kQWarps = kQThreads / 32;
 constexpr int kQBlocksPerSm = 8;  // 64 registers per thread
-constexpr size_t kQSmem = (size_t)QN * QN * sizeof(int);
+constexpr int kQueue = 64;        // surviving triangles waiting per warp
+constexpr size_t kQSmem = (size_t)QN * QN * sizeof(int) + (size_t)kQWarps * kQueue * sizeof(int);
 constexpr int kGroup = 32;        // triangles per group (one per lane)
 
 struct PackedTri {
@@ -253,10 +254,8 @@ __device__ __forceinline__ bool reaches(float4 sp, float3 p, float3 n, float R, 
 
 // Adds the count changes of triangle t's layer segments to the counters.
 __device__ __forceinline__ void add_triangle(const PackedTri *__restrict__ tris, int64_t t, float3 p,
-                                             float3 n, float R, float R2, float step, float inv_step,
-                                             int *cnt)
+                                             float3 n, float R, float step, float inv_step, int *cnt)
 {
-    if (!reaches(__ldg(&tris[t].sphere), p, n, R, R2)) return;
     const float4 a4 = __ldg(&tris[t].v0), b4 = __ldg(&tris[t].v1), c4 = __ldg(&tris[t].v2);
     float z[3];
     float3 q[3];
@@ -303,11 +302,13 @@ __device__ __forceinline__ void add_triangle(const PackedTri *__restrict__ tris,
 
 // One CTA per oriented point (persistent over points).  Each warp takes 32
 // triangle groups at a time, one per lane (interleaved with the other
-// warps' groups), and tests them against the
-// support cylinder; then, for every group that passed (a warp-wide ballot),
-// its lanes take the group's triangles, one each, and add their segments'
-// count changes to the point's 64 x 64 counters in shared memory.  The four
-// warps then turn 16 layers each into descriptor words.
+// warps' groups), and tests them against the support cylinder; for every
+// group that passed (a warp-wide ballot), its lanes test the group's
+// triangles, one each, and push the survivors onto the warp's queue in
+// shared memory; whenever 32 are waiting, every lane takes one and adds its
+// segments' count changes to the point's 64 x 64 counters, so the costly
+// part runs on full warps.  The four warps then turn 16 layers each into
+// descriptor words.
 __global__ void __launch_bounds__(kQThreads, kQBlocksPerSm)
 quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float4 *__restrict__ groups,
               int64_t n_groups, const float *__restrict__ points, const float *__restrict__ normals,
@@ -315,6 +316,8 @@ quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float4 *__re
 {
     extern __shared__ __align__(16) int cnt[];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int *queue = cnt + QN * QN + w * kQueue;
+    const uint32_t below = (1u << lane) - 1u;
     const float step = R / QN, inv_step = QN / R;
     const float R2 = R * R;
     for (int64_t j = blockIdx.x; j < np; j += gridDim.x) {
@@ -323,6 +326,7 @@ quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float4 *__re
         const float3 p = make_float3(points[j * 3], points[j * 3 + 1], points[j * 3 + 2]);
         float3 n = make_float3(normals[j * 3], normals[j * 3 + 1], normals[j * 3 + 2]);
         const float len = sqrtf(dot3(n, n));
+        int qn = 0;                      // triangles waiting in this warp's queue
         if (len > 0.f) {
             n = make_float3(n.x / len, n.y / len, n.z / len);
             // lane i of warp w tests group g0 + i * kQWarps + w: neighbouring
@@ -335,9 +339,23 @@ quicci_kernel(const PackedTri *__restrict__ tris, int64_t nt, const float4 *__re
                     const int b = __ffs(mask) - 1;
                     mask &= mask - 1;
                     const int64_t t = (g0 + (int64_t)b * kQWarps + w) * kGroup + lane;
-                    if (t < nt) add_triangle(tris, t, p, n, R, R2, step, inv_step, cnt);
+                    const bool live = t < nt && reaches(__ldg(&tris[t].sphere), p, n, R, R2);
+                    const uint32_t lm = __ballot_sync(0xffffffffu, live);
+                    if (live) queue[qn + __popc(lm & below)] = (int)t;
+                    qn += __popc(lm);
+                    __syncwarp();
+                    if (qn >= 32) {
+                        add_triangle(tris, queue[lane], p, n, R, step, inv_step, cnt);
+                        qn -= 32;
+                        __syncwarp();
+                        const int moved = lane < qn ? queue[32 + lane] : 0;
+                        __syncwarp();
+                        if (lane < qn) queue[lane] = moved;
+                        __syncwarp();
+                    }
                 }
             }
+            if (lane < qn) add_triangle(tris, queue[lane], p, n, R, step, inv_step, cnt);
         }
         __syncthreads();
         // warp w: layers 16w .. 16w + 15, lanes hold circles lane and lane + 32
