@@ -167,10 +167,12 @@ int dt_insert(dt_index *index, const uint64_t *d_new, int64_t m, void *stream);
  * memory; d_out [n_points][64] uint64 (device, 16-byte aligned).  FP32
  * arithmetic: a bit can differ from exact arithmetic only where a circle
  * passes within rounding distance of a segment's end or closest point, or a
- * layer plane within rounding distance of a vertex.  Every triangle is
- * tested against every point (bounding-sphere rejection first).  Waits on
- * the host once, to validate the triangles' vertex ids, then enqueues the
- * descriptor kernel on `stream`.
+ * layer plane within rounding distance of a vertex.  Triangles are sorted
+ * along a Morton curve and grouped by 32; every point tests every group's
+ * bounding sphere, then the triangles of the groups that reach its support
+ * cylinder.  Waits on the host once, to validate the triangles' vertex ids,
+ * then enqueues the sort and the descriptor kernel on `stream` (scratch is
+ * released on the stream after them).
  * Errors: DT_EINVAL (null or misaligned pointers, negative or too large
  * sizes, triangles without vertices, support_radius not positive and
  * finite, a vertex id outside [0, n_vertices)), DT_ENOMEM, DT_ECUDA.

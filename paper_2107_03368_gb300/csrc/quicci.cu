@@ -98,8 +98,14 @@ __device__ __forceinline__ int ordered(float f)
 }
 __device__ __forceinline__ float unordered(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
 
+__global__ void box_init_kernel(int *box)
+{
+    if (threadIdx.x < 3) box[threadIdx.x] = INT_MAX;
+    else if (threadIdx.x < 6) box[threadIdx.x] = INT_MIN;
+}
+
 // Bounding box of the triangle centres: box[0..2] min, box[3..5] max, as
-// ordered ints (box initialised to +max / -max by the host).
+// ordered ints (box_init_kernel sets the starting values).
 __global__ void centre_box_kernel(const PackedTri *__restrict__ tris, int64_t nt, int *__restrict__ box)
 {
     int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
@@ -411,8 +417,7 @@ int launch_quicci(const float *d_vertices, int64_t n_vertices, const int32_t *d_
         DT_CUDA_TRY(scratch.alloc(&val2, (size_t)nt * 4));
         DT_CUDA_TRY(scratch.alloc(&hist, (size_t)radix_tiles(nt) * 256 * 4));
         DT_CUDA_TRY(scratch.alloc(&box, 6 * sizeof(int)));
-        const int h_box[6] = {INT_MAX, INT_MAX, INT_MAX, INT_MIN, INT_MIN, INT_MIN};
-        DT_CUDA_TRY(cudaMemcpyAsync(box, h_box, sizeof(h_box), cudaMemcpyHostToDevice, s));
+        box_init_kernel<<<1, 32, 0, s>>>(box);
         const unsigned gb = (unsigned)std::min<int64_t>((nt + 255) / 256, 4096);
         centre_box_kernel<<<gb, 256, 0, s>>>(packed, nt, box);
         morton_kernel<<<gb, 256, 0, s>>>(packed, nt, box, key, val);
@@ -422,8 +427,6 @@ int launch_quicci(const float *d_vertices, int64_t n_vertices, const int32_t *d_
         group_sphere_kernel<<<(unsigned)std::min<int64_t>((n_groups + 7) / 8, 8192), 256, 0, s>>>(
             sorted, nt, n_groups, groups);
         DT_CUDA_TRY(cudaGetLastError());
-        // h_box must outlive its upload
-        DT_CUDA_TRY(cudaStreamSynchronize(s));
     }
     DT_CUDA_TRY(allow_smem((const void *)quicci_kernel, (int)kQSmem));
     const int64_t blocks = std::min<int64_t>(n_points, (int64_t)sm_count() * kQBlocksPerSm);

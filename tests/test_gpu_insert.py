@@ -132,3 +132,32 @@ def test_failed_allocation_leaves_index_unchanged():
     assert failed >= 5
     o = oracle.insert(db, oracle.build(db[:4000], 16), 4000, leaf_size=16)
     assert_same_tree(ix.export(), o)
+
+
+def test_other_entry_points_on_a_grown_tree():
+    """Voting (tree engine) and the warm-started search on a tree grown by two
+    insertions give the same results as on a tree built over everything at
+    once (both are exact)."""
+    n_obj, per = 12, 400
+    db, obj = synth.database(61, n_obj * per, per_object=per, pool=20)
+    grown = dt.dt_build(to_dev(db[:3000]), leaf_size=16)
+    dt.dt_insert(grown, to_dev(db[3000:4000]))
+    dt.dt_insert(grown, to_dev(db[4000:]))
+    fresh = dt.dt_build(to_dev(db), leaf_size=16)
+    d_obj = torch.from_numpy(obj.view(np.int32)).cuda()
+    qd, off = synth.partial_queries(62, db, n_obj, per, 6, n_min=50, n_max=400)[:2]
+    d_qd, d_off = to_dev(qd), torch.from_numpy(off).cuda()
+    for thr in (0, 5):
+        a = dt.retrieve_objects(grown, d_obj, n_obj, d_qd, d_off, thr, 3, engine=1)
+        b = dt.retrieve_objects(fresh, d_obj, n_obj, d_qd, d_off, thr, 3, engine=1)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    q = edge_queries(63, db, 50)
+    d_q = to_dev(q)
+    idx, score, ab, _ = dt.dt_search(grown, d_q, 5, with_ab=True)
+    seeds = torch.flip(idx, dims=[1]).contiguous()
+    s_idx, s_score, s_ab, _ = dt.dt_search_seeded(grown, d_q, 5, seeds, with_ab=True)
+    assert torch.equal(idx, s_idx) and torch.equal(score, s_score) and torch.equal(ab, s_ab)
+    assert_matches_oracle(db, q, 5, idx, score, ab)
+    grown.free()
+    fresh.free()
