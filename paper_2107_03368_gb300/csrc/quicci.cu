@@ -146,7 +146,7 @@ __device__ __forceinline__ uint32_t spread3(uint32_t x)
     return x;
 }
 
-// Morton key (10 bits per axis) of each triangle centre within the box.
+// Morton key (8 bits per axis, 24 in all) of each triangle centre within the box.
 __global__ void morton_kernel(const PackedTri *__restrict__ tris, int64_t nt, const int *__restrict__ box,
                               uint32_t *__restrict__ key, uint32_t *__restrict__ val)
 {
@@ -156,7 +156,7 @@ __global__ void morton_kernel(const PackedTri *__restrict__ tris, int64_t nt, co
     for (int k = 0; k < 3; ++k) {
         lo[k] = unordered(box[k]);
         const float ext = unordered(box[3 + k]) - lo[k];
-        scale[k] = ext > 0.f ? 1023.f / ext : 0.f;
+        scale[k] = ext > 0.f ? 255.f / ext : 0.f;
     }
     for (; t < nt; t += stride) {
         const float4 c = tris[t].sphere;
@@ -164,7 +164,7 @@ __global__ void morton_kernel(const PackedTri *__restrict__ tris, int64_t nt, co
         uint32_t m = 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float f = fminf(fmaxf((cc[k] - lo[k]) * scale[k], 0.f), 1023.f);
+            const float f = fminf(fmaxf((cc[k] - lo[k]) * scale[k], 0.f), 255.f);
             m |= spread3((uint32_t)f) << k;
         }
         key[t] = m;
@@ -273,10 +273,15 @@ __device__ __forceinline__ void add_triangle(const PackedTri *__restrict__ tris,
         q[i] = axpy3(-z[i], n, rel[i]);
     }
     const float zmin = fminf(z[0], fminf(z[1], z[2])), zmax = fmaxf(z[0], fmaxf(z[1], z[2]));
-    // layers with z_l in (zmin, zmax], widened by one on each side; the exact
-    // side test below decides
-    int l0 = (int)floorf((zmin + R) * (0.5f * inv_step) - 0.5f);
-    int l1 = (int)ceilf((zmax + R) * (0.5f * inv_step) - 0.5f);
+    // layers with z_l in (zmin, zmax]: z_l > zmin iff l > x0 and z_l <= zmax
+    // iff l <= x1; where rounding could put x0 or x1 on the wrong side of an
+    // integer the range takes one more layer, and the exact side test below
+    // decides
+    const float x0 = (zmin + R) * (0.5f * inv_step) - 0.5f;
+    const float x1 = (zmax + R) * (0.5f * inv_step) - 0.5f;
+    const float f0 = floorf(x0), f1 = floorf(x1);
+    int l0 = (int)f0 + (x0 - f0 > 1e-3f ? 1 : 0);
+    int l1 = (int)f1 + (x1 - f1 > 1.f - 1e-3f ? 1 : 0);
     l0 = max(l0, 0);
     l1 = min(l1, QN - 1);
     for (int l = l0; l <= l1; ++l) {
@@ -422,7 +427,7 @@ int launch_quicci(const float *d_vertices, int64_t n_vertices, const int32_t *d_
         centre_box_kernel<<<gb, 256, 0, s>>>(packed, nt, box);
         morton_kernel<<<gb, 256, 0, s>>>(packed, nt, box, key, val);
         DT_CUDA_TRY(cudaGetLastError());
-        DT_CUDA_TRY(radix_sort_pairs(&key, &val, &key2, &val2, nt, 30, hist, s));
+        DT_CUDA_TRY(radix_sort_pairs(&key, &val, &key2, &val2, nt, 24, hist, s));
         gather_tris_kernel<<<gb, 256, 0, s>>>(packed, val, nt, sorted);
         group_sphere_kernel<<<(unsigned)std::min<int64_t>((n_groups + 7) / 8, 8192), 256, 0, s>>>(
             sorted, nt, n_groups, groups);
