@@ -63,7 +63,8 @@ enum {
     DT_ENOMEM = -2,        /* device allocation failed */
     DT_ECUDA = -3,         /* a CUDA runtime call failed */
     DT_ETIMEOUT = -4,      /* a bounded device wait gave up */
-    DT_EUNSUPPORTED = -5   /* valid request this build/device cannot serve */
+    DT_EUNSUPPORTED = -5,  /* valid request this build/device cannot serve */
+    DT_EIO = -6            /* a file could not be opened, read or written */
 };
 
 /* Opaque Dissimilarity Tree index; created by dt_build, freed by dt_free. */
@@ -181,6 +182,28 @@ int quicci_generate(const float *d_vertices, int64_t n_vertices, const int32_t *
                     int64_t n_triangles, const float *d_points, const float *d_normals,
                     int64_t n_points, float support_radius, int32_t modified, uint64_t *d_out,
                     void *stream);
+
+/*
+ * Saving and loading an index (checkpoint / resume).  dt_save writes the
+ * tree of `index` — built or grown by dt_insert — to `path`: a 64-byte
+ * header (magic "DTINDEX", version 1, n, node and leaf counts, depth,
+ * leaf_size, AND images or not), the node records, the OR (and AND) images,
+ * the permutation, and a 64-bit checksum of everything after the header;
+ * little-endian.  The descriptors are not written: dt_load takes the
+ * database d_db [n][64] (device, 16-byte aligned, original-index order, the
+ * same rows the index was built and grown over) and rebuilds the
+ * tree-ordered copy on the GPU.  Before anything reaches the device,
+ * dt_load checks the header, the file size, the checksum, that the nodes
+ * form one tree rooted at node 0 whose children split their parent's
+ * segment one level below it, that leaves hold at most leaf_size
+ * descriptors, the recorded depth and leaf count, and that the permutation
+ * is one; images are taken as written.  Both are synchronous.
+ * Errors: DT_EINVAL (null arguments, n different from the file's, a
+ * rejected file — dt_last_error names the check), DT_EIO (the file cannot
+ * be opened, read or written), DT_ENOMEM, DT_ECUDA.
+ */
+int dt_save(const dt_index *index, const char *path);
+int dt_load(const char *path, const uint64_t *d_db, int64_t n, void *stream, dt_index **out);
 
 /* Shape of a built index (host call, no device work). */
 int dt_get_info(const dt_index *index, dt_index_info *info);

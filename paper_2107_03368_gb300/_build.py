@@ -28,6 +28,7 @@ CUDA_SOURCES = [
     "bf_tc.cu",
     "dt_build.cu",
     "dt_insert.cu",
+    "index_io.cu",
     "quicci.cu",
     "dt_search.cu",
     "encoder.cu",

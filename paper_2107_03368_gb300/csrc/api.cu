@@ -109,6 +109,7 @@ const char *dt_status_string(int status)
     case DT_ECUDA: return "DT_ECUDA";
     case DT_ETIMEOUT: return "DT_ETIMEOUT";
     case DT_EUNSUPPORTED: return "DT_EUNSUPPORTED";
+    case DT_EIO: return "DT_EIO";
     default: return "DT_UNKNOWN";
     }
 }

@@ -674,4 +674,20 @@ int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fu
     return DT_OK;
 }
 
+// db_tree[pos] = db[perm[pos]] and iperm = perm^-1 for an index whose perm
+// (device, n entries, a permutation of 0 .. n-1) is already in place;
+// allocates both arrays.
+int fill_index_rows(const uint64_t *db, dt_index *ix, cudaStream_t s)
+{
+    const int64_t n = ix->n;
+    DT_CUDA_TRY(cudaMalloc((void **)&ix->db_tree, (size_t)n * kWords * 8));
+    DT_CUDA_TRY(cudaMalloc((void **)&ix->iperm, (size_t)n * 4));
+    gather_rows_kernel<<<std::min<int64_t>((n + 7) / 8, 8 * 152 * 8), 256, 0, s>>>(db, ix->perm, n,
+                                                                                   ix->db_tree);
+    invert_kernel<<<std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(ix->perm, n, ix->iperm);
+    DT_CUDA_TRY(cudaGetLastError());
+    DT_CUDA_TRY(cudaStreamSynchronize(s));
+    return DT_OK;
+}
+
 }  // namespace dtk

@@ -272,6 +272,7 @@ int grow_forest(const uint64_t *db, uint32_t *perm, int64_t n_rows, const std::v
                 int leaf_size, int use_and, int fused_cap, cudaStream_t s, Grow &g_or, Grow &g_and,
                 std::vector<NodeRec> &recs, int64_t *n_leaves, int32_t *depth);
 int insert_tree(dt_index *ix, const uint64_t *d_new, int64_t m, cudaStream_t s);
+int fill_index_rows(const uint64_t *db, dt_index *ix, cudaStream_t s);
 int launch_quicci(const float *d_vertices, int64_t n_vertices, const int32_t *d_triangles,
                   int64_t n_triangles, const float *d_points, const float *d_normals,
                   int64_t n_points, float support_radius, int modified, uint64_t *d_out,

@@ -15,6 +15,7 @@ unsigned C arrays are carried in signed tensors of the same width):
 from __future__ import annotations
 
 import ctypes
+import os
 
 import torch
 
@@ -22,7 +23,7 @@ from . import _build
 
 _lib = None
 
-DT_OK, DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_ETIMEOUT, DT_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+DT_OK, DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_ETIMEOUT, DT_EUNSUPPORTED, DT_EIO = 0, -1, -2, -3, -4, -5, -6
 DT_MAX_K = 32
 WORDS = 64
 
@@ -75,6 +76,8 @@ def load():
         sig = {
             "dt_build": ([P, i64, P, P, P], ctypes.c_int),
             "dt_insert": ([P, P, i64, P], ctypes.c_int),
+            "dt_save": ([P, ctypes.c_char_p], ctypes.c_int),
+            "dt_load": ([ctypes.c_char_p, P, i64, P, P], ctypes.c_int),
             "quicci_generate": ([P, i64, P, i64, P, P, i64, ctypes.c_float, i32, P, P],
                                 ctypes.c_int),
             "dt_get_info": ([P, P], ctypes.c_int),
@@ -161,6 +164,10 @@ class Index:
         return dict(child=child, begin=begin, count=count, level=level, or_img=or_img,
                     and_img=and_img, perm=perm)
 
+    def save(self, path):
+        """Writes the tree (not the descriptors) to `path` (dt_save)."""
+        _check(load().dt_save(self.handle, os.fsencode(path)), "dt_save")
+
     def free(self):
         if self._h is not None:
             load().dt_free(self._h)
@@ -179,6 +186,16 @@ def dt_build(db, leaf_size=32, use_and_image=False, fused_cap=0, stream=None) ->
     out = ctypes.c_void_p()
     _check(load().dt_build(_ptr(db), db.shape[0], ctypes.byref(params), _stream(stream),
                            ctypes.byref(out)), "dt_build")
+    return Index(out)
+
+
+def dt_load(path, db, stream=None) -> Index:
+    """Loads a tree written by Index.save over the database `db` [n, 64]
+    (device; the rows it was built and grown over, in original-index order)."""
+    db = _desc(db, "db")
+    out = ctypes.c_void_p()
+    _check(load().dt_load(os.fsencode(path), _ptr(db), db.shape[0], _stream(stream),
+                          ctypes.byref(out)), "dt_load")
     return Index(out)
 
 
