@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -145,7 +146,7 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_r%d.csv" % os.getpid())
+        self.path = os.path.join(tempfile.gettempdir(), "dt_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
