@@ -48,7 +48,7 @@ constexpr int kGroup = 32;        // triangles per group (one per lane)
 
 struct PackedTri {
     float4 v0, v1, v2;            // xyz, w unused
-    float4 sphere;                // centre xyz, radius (negative: skip)
+    float4 sphere;                // centre xyz, radius (negative: a bad vertex id, call rejected)
 };
 
 // Gathers each triangle's vertices and bounding sphere; flags ids out of range.
