@@ -31,9 +31,11 @@
  * Memory: every pointer named d_* is CUDA device memory owned by the caller
  *   and must stay valid until the stream reaches the call's end.  The
  *   library owns dt_index objects and any scratch space it allocates.
- *   Scratch comes from the device's default stream-ordered memory pool;
- *   on first use of a device the library raises that pool's release
- *   threshold to 16 GiB, so freed scratch stays cached between calls.
+ *   Scratch comes from a stream-ordered memory pool that the library
+ *   creates for each device on first use and keeps until the process
+ *   exits; its release threshold is 16 GiB, so freed scratch stays cached
+ *   between calls.  The device's default pool and its settings are left
+ *   alone.  Under stream capture scratch is allocated by the graph.
  * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
  *   enqueue their work and return; outputs are ready when the stream is.
  *   dt_build and calls that return host statistics synchronise the stream.
@@ -294,7 +296,15 @@ int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, 
  *   the part it uses with the empty pattern (a stream-ordered memset, no
  *   allocation).  Calls whose work overlaps on the GPU (e.g. on two
  *   unordered streams) race on it; order them on one stream.
- * Results are identical to bf_search's.  Errors: DT_EINVAL, DT_ECUDA.
+ * Results are identical to bf_search's.
+ * Errors: DT_EINVAL (bad arguments, or a request larger than the fixed
+ * scratch), DT_EUNSUPPORTED (device ordinal 64 or above), DT_ECUDA.  A
+ * device wait that gave up is not reported by this call: the kernel raises
+ * the same device-side flag as bf_search's popcount path, and the next
+ * dt_sync_status returns DT_ETIMEOUT.  That status covers every search
+ * enqueued since the previous dt_sync_status, so it cannot tell which call
+ * timed out; call dt_sync_status right after this one to attribute it.
+ * Nothing in this call touches a memory pool or its settings.
  */
 #define DT_NOALLOC_SCRATCH_BYTES (16u << 20)
 int bf_search_noalloc(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,

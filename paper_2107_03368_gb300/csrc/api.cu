@@ -25,18 +25,44 @@ int sm_count()
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         cached[dev] = v > 0 ? v : 1;
-        // Scratch comes from the stream-ordered allocator; by default its
-        // pool hands freed memory back to the system at every
-        // synchronisation, so the next call maps it again.  Keep up to
-        // 16 GiB cached in the device's default pool instead.
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-            uint64_t keep = 16ull << 30;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        }
         cudaGetLastError();
     }
     return cached[dev];
+}
+
+// The library's own stream-ordered memory pool on the current device,
+// created on first use and kept until the process exits.  Its release
+// threshold is 16 GiB, so scratch freed by one call is reused by the next
+// instead of being unmapped at every synchronisation.  A pool of its own
+// leaves the caller's default pool and its settings untouched.
+static cudaError_t library_pool(cudaMemPool_t *out)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = 16ull << 30;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
 }
 
 cudaError_t allow_smem(const void *func, int bytes)
@@ -66,7 +92,18 @@ cudaError_t dt_malloc_async(void **p, size_t bytes, cudaStream_t s)
         *p = nullptr;
         return cudaErrorMemoryAllocation;
     }
-    return cudaMallocAsync(p, bytes, s);
+    // Under stream capture the allocation becomes a node of the graph and
+    // its memory belongs to the graph, whichever pool is named.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusNone;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = library_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 // A device (or managed) allocation; host pointers would make kernels fault.

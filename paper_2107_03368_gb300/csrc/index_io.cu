@@ -14,9 +14,12 @@
 // GPU: sizes, the checksum, that the nodes form one tree whose children
 // partition their parent's segment and sit one level below it, that leaves
 // hold at most leaf_size descriptors, the recorded depth and leaf count, and
-// that the permutation is one.  The images are taken as written (the
-// checksum guards them against damage); images that do not cover their
-// descriptors could make a search inexact, never read out of bounds.
+// that the permutation is one.  Once the tree-ordered rows are on the GPU,
+// one more pass checks the images against them (check_images_kernel): a
+// file loaded over a database other than the one it was built over (other
+// rows, or the same rows in another order) is rejected, because its images
+// would no longer bound their subtrees and searches could silently miss
+// results.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -234,6 +237,70 @@ int read_index(const char *path, int64_t n, LoadedIndex *L)
     return check_tree(*L);
 }
 
+// One warp per node (a lane owns 16 bytes of each image): a leaf's stored
+// images must equal the OR and AND of its rows of the tree-ordered
+// database, an inner node's the OR and AND of its two children's stored
+// images.  By induction from the leaves every image is then exactly that of
+// its node's descriptors.  The tree's shape was checked on the host, so
+// every segment and child id is in range.  Sets *bad on any difference.
+__global__ void check_images_kernel(const NodeRec *__restrict__ node, int64_t n_nodes,
+                                    const uint64_t *__restrict__ db_tree,
+                                    const uint64_t *__restrict__ or_img,
+                                    const uint64_t *__restrict__ and_img, uint32_t *__restrict__ bad)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (; i < n_nodes; i += stride) {
+        const NodeRec r = node[i];
+        uint4 o, a;
+        if (r.first_child < 0) {
+            o = make_uint4(0u, 0u, 0u, 0u);
+            a = make_uint4(~0u, ~0u, ~0u, ~0u);
+            for (int j = 0; j < r.count; ++j) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(db_tree + ((int64_t)r.begin + j) * kWords) + lane);
+                o.x |= v.x; o.y |= v.y; o.z |= v.z; o.w |= v.w;
+                a.x &= v.x; a.y &= v.y; a.z &= v.z; a.w &= v.w;
+            }
+        } else {
+            const int64_t c = r.first_child;
+            const uint4 s0 = __ldg(reinterpret_cast<const uint4 *>(or_img + c * kWords) + lane);
+            const uint4 s1 = __ldg(reinterpret_cast<const uint4 *>(or_img + (c + 1) * kWords) + lane);
+            o = make_uint4(s0.x | s1.x, s0.y | s1.y, s0.z | s1.z, s0.w | s1.w);
+            if (and_img) {
+                const uint4 t0 = __ldg(reinterpret_cast<const uint4 *>(and_img + c * kWords) + lane);
+                const uint4 t1 = __ldg(reinterpret_cast<const uint4 *>(and_img + (c + 1) * kWords) + lane);
+                a = make_uint4(t0.x & t1.x, t0.y & t1.y, t0.z & t1.z, t0.w & t1.w);
+            }
+        }
+        const uint4 so = __ldg(reinterpret_cast<const uint4 *>(or_img + i * kWords) + lane);
+        bool diff = so.x != o.x || so.y != o.y || so.z != o.z || so.w != o.w;
+        if (and_img) {
+            const uint4 sa = __ldg(reinterpret_cast<const uint4 *>(and_img + i * kWords) + lane);
+            diff = diff || sa.x != a.x || sa.y != a.y || sa.z != a.z || sa.w != a.w;
+        }
+        if (__any_sync(0xffffffffu, diff) && lane == 0) atomicOr(bad, 1u);
+    }
+}
+
+int check_images(const dt_index *ix, cudaStream_t s)
+{
+    Scratch scratch(s);
+    uint32_t *bad = nullptr;
+    DT_CUDA_TRY(scratch.alloc(&bad, 4));
+    DT_CUDA_TRY(cudaMemsetAsync(bad, 0, 4, s));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((ix->n_nodes + 7) / 8, (int64_t)sm_count() * 16));
+    check_images_kernel<<<(unsigned)blocks, 256, 0, s>>>(ix->node, ix->n_nodes, ix->db_tree, ix->or_img,
+                                                         ix->and_img, bad);
+    DT_CUDA_TRY(cudaGetLastError());
+    uint32_t h = 0;
+    DT_CUDA_TRY(cudaMemcpyAsync(&h, bad, 4, cudaMemcpyDeviceToHost, s));
+    DT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) return bad_file("node images do not match the database rows (a different database, "
+                           "or its rows in another order, than the index was built over)");
+    return DT_OK;
+}
+
 int upload_index(const LoadedIndex &L, const uint64_t *d_db, cudaStream_t s, dt_index **out)
 {
     dt_index *ix = new dt_index();
@@ -262,7 +329,9 @@ int upload_index(const LoadedIndex &L, const uint64_t *d_db, cudaStream_t s, dt_
     }
     DT_CUDA_TRY(cudaMalloc((void **)&ix->perm, L.perm.size() * 4));
     DT_CUDA_TRY(cudaMemcpy(ix->perm, L.perm.data(), L.perm.size() * 4, cudaMemcpyHostToDevice));
-    const int rc = fill_index_rows(d_db, ix, s);
+    int rc = fill_index_rows(d_db, ix, s);
+    if (rc != DT_OK) return rc;
+    rc = check_images(ix, s);
     if (rc != DT_OK) return rc;
     *out = ix;
     ix = nullptr;                      // ownership passes to the caller

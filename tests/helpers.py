@@ -59,3 +59,37 @@ def assert_matches_oracle(db, q, k, idx, score, ab=None, oidx=None):
         g_ab = u16_np(ab)
         exp_ab = np.where(o_ab < 0, 0xFFFF, o_ab)
         assert np.array_equal(g_ab, exp_ab), "A/B counts differ from the oracle"
+
+
+def assert_each_result_exact(db, q, idx, score, rows=None):
+    """Every reported result is exact for its own row, whatever the search
+    examined: the index is a database row, the FP32 score is that row's
+    Eq. 1 distance to the query (the oracle's FP64 value, within SCORE_RTOL;
+    exactly 0 for distance 0), and each query's list is strictly ascending in
+    (exact distance, index) — distances compared as exact rationals A/P + B/Z
+    — with padding (0xFFFFFFFF, +inf) only after the valid results."""
+    from fractions import Fraction
+    g_idx = idx_np(idx)
+    g_s = score.cpu().numpy().astype(np.float64)
+    rows = range(q.shape[0]) if rows is None else rows
+    n = db.shape[0]
+    for r in rows:
+        pq = int(np.unpackbits(np.ascontiguousarray(q[r]).view(np.uint8)).sum())
+        P, Z = max(pq, 1), max(4096 - pq, 1)
+        prev, padded = None, False
+        for j in range(g_idx.shape[1]):
+            t = int(g_idx[r, j])
+            if t == 0xFFFFFFFF:
+                assert np.isinf(g_s[r, j]), (r, j)
+                padded = True
+                continue
+            assert not padded, "valid result after padding in row %d" % r
+            assert 0 <= t < n, (r, j, t)
+            d, a, b = oracle.wh(q[r], db[t])
+            if d == 0.0:
+                assert g_s[r, j] == 0.0, (r, j)
+            else:
+                assert abs(g_s[r, j] - d) <= SCORE_RTOL * d, (r, j, g_s[r, j], d)
+            key = (Fraction(a, P) + Fraction(b, Z), t)
+            assert prev is None or prev < key, "row %d not ascending at %d" % (r, j)
+            prev = key

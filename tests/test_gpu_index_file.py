@@ -44,3 +44,28 @@ def test_save_load_roundtrip(tmp_path, grown, use_and):
     assert e.value.status == dt.DT_EINVAL
     ix.free()
     back.free()
+
+
+def test_load_over_other_rows_is_rejected(tmp_path):
+    """The file keeps the images, not the descriptors: loading it over a
+    database of the same size but other contents (here the same rows in
+    another order, and one row set to all ones) must be refused, since its images
+    would no longer bound their subtrees."""
+    db = mixed_db(73, 3000)
+    d_db = to_dev(db)
+    ix = dt.dt_build(d_db, leaf_size=16, use_and_image=True)
+    path = tmp_path / "tree.dtix"
+    ix.save(path)
+    rng = np.random.default_rng(0)
+    changed = db.copy()
+    changed[1234] = np.uint64(0xFFFFFFFFFFFFFFFF)     # widens its leaf's OR image
+    for other in (db[rng.permutation(db.shape[0])], changed):
+        with pytest.raises(dt.DtError) as e:
+            dt.dt_load(path, to_dev(other))
+        assert e.value.status == dt.DT_EINVAL
+        assert "images" in dt.dt_last_error()
+    back = dt.dt_load(path, d_db)          # the right rows still load
+    assert back.info() == ix.info()
+    ix.free()
+    back.free()
+

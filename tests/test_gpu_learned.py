@@ -13,7 +13,7 @@ import pytest
 import torch
 
 import oracle
-from helpers import idx_np, mixed_db, to_dev
+from helpers import assert_each_result_exact, idx_np, mixed_db, to_dev
 from oracle import encoder as oe
 from paper_2107_03368_gb300 import dt, learned, synth
 
@@ -114,6 +114,14 @@ def test_ivf_all_lists_is_exact_and_few_lists_never_beat_exact(path):
     hit = idx_np(idx4)[:, 0] == o_idx[:, 0]
     assert np.all(np.abs(s4[hit] - o_score[hit, 0]) <= 1e-6 * o_score[hit, 0] + 1e-12)
     assert np.all(sc4.cpu().numpy() < db.shape[0])
+    # partial probes, k = 5: every returned row, hit or not, carries its own
+    # exact distance, in (distance, index) order
+    assert_each_result_exact(db, q, idx4, score4)
+    idx5, score5, _ = ivf.search(d_q, 5, n_probe=4, with_scanned=True, path=path)
+    assert_each_result_exact(db, q, idx5, score5)
+    s5 = score5.cpu().numpy()
+    fin = np.isfinite(s5)
+    assert np.all(s5[fin] >= np.broadcast_to(o_score, s5.shape)[fin] * (1 - 1e-6))
 
 
 def test_learned_proposal_gains_over_plain_tree_search():
@@ -170,13 +178,13 @@ def test_ivf_list_major_tensor_path_equals_per_query_path(k, n_probe):
     assert torch.equal(a[2], b[2])
     sample = np.arange(0, 3000, 97)
     o_idx, o_score, _ = oracle.bf_topk(db, q[sample], k)
-    got = idx_np(b[0])[sample]
     s = b[1].cpu().numpy()[sample]
-    # every reported result is exact for its row: score equals the oracle's
-    # distance of that descriptor, and no result beats the exact k-th
-    assert np.all(s[:, -1] >= o_score[:, -1] * (1 - 1e-6))
-    assert np.all(np.diff(s, axis=1) >= 0)
-    del got
+    # every reported result is exact for its row: its score is the oracle's
+    # distance of that descriptor, rows ascend in (distance, index), and no
+    # result beats the exact result of the same rank
+    assert_each_result_exact(db, q, b[0], b[1], rows=sample)
+    fin = np.isfinite(s)
+    assert np.all(s[fin] >= o_score[fin] * (1 - 1e-6))
 
 
 def test_ivf_edges_on_both_paths():
