@@ -227,13 +227,32 @@ int dt_export(const dt_index *index, int64_t *h_child, int64_t *h_begin, int64_t
  * dt_search — exact k nearest database descriptors of each query by
  * Dissimilarity Tree traversal (§4.2).  A subtree is skipped only when its
  * bound, popc(q & ~OR) * Z (+ popc(~q & AND) * P with AND images), is
- * strictly greater than the current k-th result's A*Z + B*P, so the result
- * equals bf_search's, ties included.
+ * strictly greater than a key known to be >= the query's k-th result's
+ * A*Z + B*P, so the result equals bf_search's, ties included.
+ *
+ * Two traversals, chosen by batch size (dt_search_path picks explicitly):
+ *   per query (fewer than 64 queries): a warp per query walks the tree
+ *     depth first with the bound of every node (dt_stats counts its nodes,
+ *     leaves, descriptors and bounds);
+ *   batched (64 or more): every query first descends greedily to one leaf
+ *     and scans it, which gives a cap >= its k-th key; queries are sorted
+ *     by the position of that leaf and grouped 256 at a time; the tensor
+ *     cores bound every (group, run of 128 tree-ordered rows) by the run's
+ *     OR image, scan exactly the runs some query of the group may need
+ *     (skipping the 128-bit chunks in which the run has no bit) and keep
+ *     per query the keys <= its cap.  The AND image is not used there (a
+ *     weaker bound, still exact).  dt_stats: nodes_visited and
+ *     bounds_evaluated count the descents plus one bound per (query, run);
+ *     leaves_visited counts the descents' leaves; descs_scanned counts the
+ *     descents' rows plus every (query, row) pair of the runs scanned for
+ *     its group.
  *
  * d_q: [nq][64] queries.  d_idx, d_score: [nq][k].  d_ab: [nq][k][2] or NULL.
  * h_stats: NULL, or host struct receiving totals over all queries (this
- * synchronises the stream).  nq = 0 is a no-op.
- * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_ETIMEOUT.
+ * synchronises the stream).  nq = 0 is a no-op.  The current device must
+ * be the index's.
+ * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA; a device wait that gave up is
+ * reported by the next dt_sync_status (DT_ETIMEOUT).
  */
 int dt_search(const dt_index *index, const uint64_t *d_q, int64_t nq, int32_t k,
               uint32_t *d_idx, float *d_score, uint16_t *d_ab, dt_stats *h_stats,
@@ -252,10 +271,22 @@ int dt_search(const dt_index *index, const uint64_t *d_q, int64_t nq, int32_t k,
  * index >= n) means "no candidate"; duplicates count once.  n_seed in
  * [0, 4096]; n_seed = 0 is plain dt_search.  Fewer than k valid distinct
  * candidates give no cap.  Other arguments, outputs and errors as dt_search.
+ * In the batched traversal the candidates join the descent's leaf in the
+ * cap, so a good proposal prunes runs of rows for whole groups of queries.
  */
 int dt_search_seeded(const dt_index *index, const uint64_t *d_q, int64_t nq, int32_t k,
                      const uint32_t *d_seed, int32_t n_seed, uint32_t *d_idx, float *d_score,
                      uint16_t *d_ab, dt_stats *h_stats, void *stream);
+
+/*
+ * dt_search_path — dt_search_seeded with the traversal chosen by the
+ * caller: path 0 = automatic (as dt_search), 1 = per query, 2 = batched.
+ * All paths give identical results.  d_seed may be NULL when n_seed = 0.
+ * Errors: as dt_search, and DT_EINVAL for another path.
+ */
+int dt_search_path(const dt_index *index, const uint64_t *d_q, int64_t nq, int32_t k,
+                   const uint32_t *d_seed, int32_t n_seed, uint32_t *d_idx, float *d_score,
+                   uint16_t *d_ab, dt_stats *h_stats, int32_t path, void *stream);
 
 /*
  * bf_search — exact k nearest database descriptors by scanning all of them

@@ -259,42 +259,57 @@ int dt_export(const dt_index *ix, int64_t *h_child, int64_t *h_begin, int64_t *h
     return DT_OK;
 }
 
-int dt_search(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k, uint32_t *d_idx,
-              float *d_score, uint16_t *d_ab, dt_stats *h_stats, void *stream)
-{
-    g_last_error.clear();
-    DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
-    if (int r = check_k(k)) return r;
-    DT_CHECK_ARG(nq >= 0 && nq < (1LL << 31), "nq out of range");
-    if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
-    if (nq == 0) return DT_OK;
-    REQUIRE_DEV(d_q, "d_q");
-    REQUIRE_DEV(d_idx, "d_idx");
-    REQUIRE_DEV(d_score, "d_score");
-    if (d_ab) REQUIRE_DEV(d_ab, "d_ab");
-    return launch_dt_search(ix, d_q, nq, k, d_idx, d_score, d_ab, h_stats, (cudaStream_t)stream);
-}
-
-int dt_search_seeded(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k,
-                     const uint32_t *d_seed, int32_t n_seed, uint32_t *d_idx, float *d_score,
-                     uint16_t *d_ab, dt_stats *h_stats, void *stream)
+// Both traversals give identical results; the batched one shares each scan
+// of the database among tiles of queries and wins from a few dozen queries.
+static int search_any(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k,
+                      const uint32_t *d_seed, int32_t n_seed, uint32_t *d_idx, float *d_score,
+                      uint16_t *d_ab, dt_stats *h_stats, int32_t path, void *stream)
 {
     g_last_error.clear();
     DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
     if (int r = check_k(k)) return r;
     DT_CHECK_ARG(nq >= 0 && nq < (1LL << 31), "nq out of range");
     DT_CHECK_ARG(n_seed >= 0 && n_seed <= 4096, "n_seed must be in [0, 4096]");
+    DT_CHECK_ARG(path >= 0 && path <= 2, "path must be 0, 1 or 2");
     if (h_stats) std::memset(h_stats, 0, sizeof(*h_stats));
     if (nq == 0) return DT_OK;
     REQUIRE_DEV(d_q, "d_q");
     REQUIRE_DEV(d_idx, "d_idx");
     REQUIRE_DEV(d_score, "d_score");
     if (d_ab) REQUIRE_DEV(d_ab, "d_ab");
-    if (n_seed == 0)
-        return launch_dt_search(ix, d_q, nq, k, d_idx, d_score, d_ab, h_stats, (cudaStream_t)stream);
-    REQUIRE_DEV(d_seed, "d_seed");
-    return launch_dt_search_seeded(ix, d_q, nq, k, d_seed, n_seed, d_idx, d_score, d_ab, h_stats,
-                                   (cudaStream_t)stream);
+    if (n_seed > 0) REQUIRE_DEV(d_seed, "d_seed");
+    else d_seed = nullptr;
+    int dev = -1;
+    DT_CUDA_TRY(cudaGetDevice(&dev));
+    DT_CHECK_ARG(dev == ix->device, "the current device must be the index's device");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (path == 2 || (path == 0 && nq >= 64))
+        return launch_dt_search_batched(ix, d_q, nq, k, d_seed, n_seed, d_idx, d_score, d_ab,
+                                        h_stats, s);
+    if (d_seed)
+        return launch_dt_search_seeded(ix, d_q, nq, k, d_seed, n_seed, d_idx, d_score, d_ab,
+                                       h_stats, s);
+    return launch_dt_search(ix, d_q, nq, k, d_idx, d_score, d_ab, h_stats, s);
+}
+
+int dt_search(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k, uint32_t *d_idx,
+              float *d_score, uint16_t *d_ab, dt_stats *h_stats, void *stream)
+{
+    return search_any(ix, d_q, nq, k, nullptr, 0, d_idx, d_score, d_ab, h_stats, 0, stream);
+}
+
+int dt_search_seeded(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k,
+                     const uint32_t *d_seed, int32_t n_seed, uint32_t *d_idx, float *d_score,
+                     uint16_t *d_ab, dt_stats *h_stats, void *stream)
+{
+    return search_any(ix, d_q, nq, k, d_seed, n_seed, d_idx, d_score, d_ab, h_stats, 0, stream);
+}
+
+int dt_search_path(const dt_index *ix, const uint64_t *d_q, int64_t nq, int32_t k,
+                   const uint32_t *d_seed, int32_t n_seed, uint32_t *d_idx, float *d_score,
+                   uint16_t *d_ab, dt_stats *h_stats, int32_t path, void *stream)
+{
+    return search_any(ix, d_q, nq, k, d_seed, n_seed, d_idx, d_score, d_ab, h_stats, path, stream);
 }
 
 int bf_search(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int64_t nq, int32_t k,
@@ -394,6 +409,8 @@ void dt_free(dt_index *ix)
     cudaFree(ix->or_img);
     cudaFree(ix->and_img);
     cudaFree(ix->node);
+    cudaFree(ix->tile_or);
+    cudaFree(ix->tile_kmask);
     cudaSetDevice(cur);
     delete ix;
 }

@@ -110,6 +110,11 @@ bf_popc_kernel(const uint64_t *__restrict__ db, int64_t n, const uint64_t *__res
         if (__syncthreads_or(!arrived)) {      // give up together, after our copies land
             if (tid == 0) {
                 atomicOr(err, 1u);
+                // A copy that was issued but is only slow could still write
+                // shared memory after the block exits: wait for it again
+                // (bounded), and for the next tile's copy issued above.
+                if (tile - tile_begin != drop_rel_tile)
+                    mbar_wait(&sm.bar[buf], (uint32_t)((it >> 1) & 1));
                 if (tile + 1 < tile_end) mbar_wait(&sm.bar[buf ^ 1], (uint32_t)(((it + 1) >> 1) & 1));
             }
             return;

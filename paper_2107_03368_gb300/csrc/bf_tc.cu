@@ -75,19 +75,37 @@ struct TcCtl {
 };
 
 constexpr size_t STAGE_BYTES = (size_t)STAGES * STAGE;
-// + |t| halves [2 tiles][2 halves][TN] and their 32-row minima [2][2][TN / 32]
-constexpr size_t SMEM_BYTES = STAGE_BYTES + sizeof(TcCtl) + 2 * 2 * TN * 4 + 2 * 2 * (TN / 32) * 4 + 1024;
+// Kernel modes: the plain sequential search (split or list mode), the scan
+// pass of the batched tree search (need bitmap, K-chunk masks, caps) and
+// its bound pass.  Each is its own instantiation, so the plain search
+// carries none of the others' code.
+enum { MODE_PLAIN = 0, MODE_TREE = 1, MODE_BOUND = 2 };
+
+// |t| of the rows of the last tp_ring(MODE) tiles: producers write a tile's
+// |t| at its last chunk and the epilogue reads it once the tile's
+// accumulator is full.  With whole 32-chunk tiles the producers can be at
+// most one tile past the slowest epilogue warp's other buffer, so two
+// entries do.  With K chunks skipped (tree mode) a tile can be a single
+// chunk: the producers can then finish up to STAGES tiles past the one the
+// MMA waits to start, which is two past the slowest epilogue warp's, so
+// STAGES + 2 entries are in use at most.
+__host__ __device__ constexpr int tp_ring(int mode) { return mode == MODE_TREE ? 8 : 2; }
+static_assert(tp_ring(MODE_TREE) >= STAGES + 2, "|t| ring of the tree mode");
+// + |t| halves [ring][2 halves][TN] and their 32-row minima [ring][2][TN / 32]
+__host__ __device__ constexpr size_t smem_bytes(int mode)
+{
+    return STAGE_BYTES + sizeof(TcCtl) + (size_t)tp_ring(mode) * 2 * TN * 4 +
+           (size_t)tp_ring(mode) * 2 * (TN / 32) * 4 + 1024;
+}
 
 __device__ uint32_t g_tc_error;  // a bounded wait gave up (DT_ETIMEOUT)
 
 // Bit j of each byte of w -> four E4M3 bytes, 0x08 (2^-6) where the bit is
-// set: shift bit j to the byte's sign position, let prmt replicate each
-// byte's sign bit over the byte (selector nibbles 0x8-0xB), keep 0x08.
+// set: one shift moves bit j of every byte to bit 3 of that byte, one AND
+// keeps it (j is a constant at every call, so two instructions a word).
 __device__ __forceinline__ uint32_t bitplane_e4m3(uint32_t w, int j)
 {
-    uint32_t r;
-    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(w << (7 - j)));
-    return r & 0x08080808u;
+    return (j <= 3 ? (w << (3 - j)) : (w >> (j - 3))) & 0x08080808u;
 }
 
 // 32 bits -> 32 E4M3 bytes as two 16-byte pieces.  Output byte 4j + m holds
@@ -159,7 +177,8 @@ __global__ void widen_queries_kernel(const uint64_t *__restrict__ q, int64_t nq,
 
 // Gathered query tiles: row r of tile mt is query slot_q[mt * TM + r];
 // padding rows (negative) are not written (their accumulator rows are
-// never read), nor are tiles at or beyond *n_tiles.
+// never read), nor are tiles at or beyond *n_tiles (all max_tiles tiles
+// when n_tiles is null).
 __global__ void widen_gather_kernel(const uint64_t *__restrict__ q, const int32_t *__restrict__ slot_q,
                                     const int64_t *__restrict__ n_tiles, int64_t max_tiles,
                                     unsigned char *__restrict__ a_exp, uint32_t *__restrict__ qpop)
@@ -169,7 +188,7 @@ __global__ void widen_gather_kernel(const uint64_t *__restrict__ q, const int32_
     const int c = (int)(id % NCHUNK);
     const int row = (int)((id / NCHUNK) % TM);
     const int64_t mt = id / ((int64_t)NCHUNK * TM);
-    if (mt >= *n_tiles) return;
+    if (n_tiles && mt >= *n_tiles) return;
     const int32_t qi = slot_q[mt * TM + row];
     if (qi < 0) return;
     const uint4 bits = __ldg(reinterpret_cast<const uint4 *>(q + (int64_t)qi * kWords) + c);
@@ -229,6 +248,23 @@ struct TcArgs {
     const int64_t *n_units;
     uint64_t *partial;               // split mode: [n_split][nq][k]; list mode: [slot][k]
     uint32_t *err;
+    // Batched tree search (split mode only; all null otherwise):
+    //   need      bit (pair mp, scan tile g) at need[mp * need_words + g / 32]:
+    //             only tiles whose bit is set are multiplied
+    //   kmask     per scan tile, the 128-bit K chunks with any bit in the
+    //             tile: the others contribute nothing and are skipped
+    //   cap       per query row, a key >= its exact k-th result's key: larger
+    //             keys are not kept, and in bound mode it is the threshold
+    //   mode      0 = top-k lists; 1 = bound pass: the "database" rows are
+    //             tile images, row g's bound popc(q & ~image) * Z is compared
+    //             with the cap and need_out bit (mp, g) is set if some query
+    //             of the pair may need scan tile g
+    const uint32_t *need;
+    int64_t need_words;
+    const uint32_t *kmask;
+    const uint32_t *cap;
+    uint32_t *need_out;
+    int mode;
 };
 
 // One work unit: query tiles mt[0], mt[1] (mt[1] < 0: absent) against
@@ -237,6 +273,7 @@ struct TcArgs {
 struct Unit {
     int64_t mt[QT];
     int64_t r0, r1, ntiles, sp, out_base;
+    int64_t mp, t0;                  // split mode: query-tile pair, first global tile
     int nvalid[QT];
 };
 
@@ -251,14 +288,18 @@ __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
         v.r1 = t.row1;
         v.ntiles = (t.row1 - t.row0 + TN - 1) / TN;
         v.sp = 0;
+        v.mp = 0;
+        v.t0 = 0;
         v.out_base = t.out_base;
         v.nvalid[0] = t.nvalid0;
         v.nvalid[1] = t.a_tile1 >= 0 ? t.nvalid1 : 0;
     } else {
         const int64_t mp = u % a.n_mpairs;
         v.sp = u / a.n_mpairs;
+        v.mp = mp;
         v.out_base = 0;
         const int64_t t0 = v.sp * a.tiles_per_split;
+        v.t0 = t0;
         const int64_t t1 = min(a.n_ntiles, t0 + a.tiles_per_split);
         v.r0 = t0 * TN;
         v.r1 = a.n;
@@ -278,12 +319,42 @@ __device__ __forceinline__ int64_t unit_count(const TcArgs &a)
     return a.units ? *a.n_units : (int64_t)a.n_mpairs * a.n_split;
 }
 
-// The first unit at or after u (in steps of the grid) that has rows.
+// The first tile at or after local tile lt of unit uv that is multiplied
+// (every tile without a need bitmap); uv.ntiles if none is left.
+template <int MODE>
+__device__ __forceinline__ int64_t next_tile(const TcArgs &a, const Unit &uv, int64_t lt)
+{
+    if (MODE != MODE_TREE || !a.need) return lt;
+    const uint32_t *row = a.need + uv.mp * a.need_words;
+    while (lt < uv.ntiles) {
+        const int64_t g = uv.t0 + lt;
+        const uint32_t w = __ldg(row + (g >> 5)) >> (g & 31);
+        if (w) {
+            lt += __ffs(w) - 1;
+            break;
+        }
+        lt += 32 - (g & 31);
+    }
+    return lt < uv.ntiles ? lt : uv.ntiles;
+}
+
+// K chunks of local tile lt that are multiplied (never empty: a tile
+// whose image is empty still runs chunk 0, so its accumulator is zeroed).
+template <int MODE>
+__device__ __forceinline__ uint32_t chunk_mask(const TcArgs &a, const Unit &uv, int64_t lt)
+{
+    if (MODE != MODE_TREE || !a.kmask) return 0xFFFFFFFFu;
+    const uint32_t m = __ldg(a.kmask + uv.t0 + lt);
+    return m ? m : 1u;
+}
+
+// The first unit at or after u (in steps of the grid) with a tile to multiply.
+template <int MODE>
 __device__ __forceinline__ int64_t next_busy(const TcArgs &a, int64_t u, int64_t total, Unit &uv)
 {
     for (; u < total; u += gridDim.x) {
         uv = get_unit(a, u);
-        if (uv.ntiles > 0) break;
+        if (uv.ntiles > 0 && next_tile<MODE>(a, uv, 0) < uv.ntiles) break;
     }
     return u;
 }
@@ -316,6 +387,7 @@ __device__ __noinline__ uint64_t list_insert(uint64_t *L, int k, uint32_t key, i
     return L[k - 1];
 }
 
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -324,10 +396,11 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
     unsigned char *stageA = smem;                                   // [STAGES][QT][A_STAGE]
     unsigned char *stageB = smem + (size_t)STAGES * QT * A_STAGE;   // [STAGES][B_STAGE]
     TcCtl *ctl = reinterpret_cast<TcCtl *>(smem + STAGE_BYTES);
-    // |t| of each row as two half-row sums [tile & 1][half][TN], and the
-    // smallest half sum of each 32 rows [tile & 1][half][TN / 32]
+    // |t| of each row as two half-row sums [tile % TP_RING][half][TN], and
+    // the smallest half sum of each 32 rows [tile % TP_RING][half][TN / 32]
     uint32_t *tpop_s = reinterpret_cast<uint32_t *>(smem + STAGE_BYTES + sizeof(TcCtl));
-    uint32_t *tmin_s = tpop_s + 2 * 2 * TN;
+    constexpr int TP_RING = tp_ring(MODE);
+    uint32_t *tmin_s = tpop_s + TP_RING * 2 * TN;
     uint32_t *err = args.err;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -358,33 +431,56 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
     if (warp >= EPI_WARPS && warp < MMA_WARP) {
         // ------------------------------------------------ producers
         // Half a database row per thread (warps 8-11 the first 8 bytes of each
-        // chunk, warps 12-15 the second).  Bits are loaded 32 bytes (four
-        // half-chunks) at a time, one group ahead of the chunks being widened;
-        // |t| is summed on the way and left in shared memory for the epilogue.
+        // chunk, warps 12-15 the second).  Chunks are visited in groups of
+        // four consecutive chunk indices; a group is loaded (32 bytes a
+        // thread) one group ahead of the one being widened, and only the
+        // chunks of the tile's mask are widened and handed to the MMA.  |t|
+        // is summed on the way (skipped chunks hold no bit of any row of the
+        // tile) and left in shared memory for the epilogue.
         const int pw = warp - EPI_WARPS;
         const int rg = pw & 3, hw = pw >> 2;
         const int row = rg * 32 + lane;
         constexpr int G = 4;                       // chunks per load group
         uint32_t g = 0, tile = 0, tp_acc = 0;
         Unit uv{};
-        int64_t u = next_busy(args, blockIdx.x, total_units, uv), lt = 0;
+        int64_t u = next_busy<MODE>(args, blockIdx.x, total_units, uv), lt = 0;
+        uint32_t km = 0;
         int grp = 0;
+        // first group of the mask at or after group gi, or NCHUNK / G
+        auto first_group = [](uint32_t m, int gi) {
+            if (MODE != MODE_TREE) return gi < NCHUNK / G ? gi : NCHUNK / G;
+            const uint32_t rest = gi < NCHUNK / G ? m >> (gi * G) : 0u;
+            return rest ? gi + (__ffs(rest) - 1) / G : NCHUNK / G;
+        };
+        if (u < total_units) {
+            lt = next_tile<MODE>(args, uv, 0);
+            km = chunk_mask<MODE>(args, uv, lt);
+            grp = first_group(km, 0);
+        }
         uint2 nx[G];
 #pragma unroll
         for (int i = 0; i < G; ++i)
-            nx[i] = u < total_units ? load_half(args, uv, 0, row, hw, i) : make_uint2(0, 0);
+            nx[i] = u < total_units ? load_half(args, uv, lt, row, hw, grp * G + i) : make_uint2(0, 0);
         while (u < total_units) {
             const int64_t mt0 = uv.mt[0], mt1 = uv.mt[1];
             const int cur_grp = grp;
+            const uint32_t cur_km = km;
+            const int last_c = MODE == MODE_TREE ? 31 - __clz(cur_km) : NCHUNK - 1;
             uint2 cu[G];
 #pragma unroll
             for (int i = 0; i < G; ++i) cu[i] = nx[i];
-            // advance (u, lt, grp) and prefetch the next group
-            if (++grp == NCHUNK / G) {
-                grp = 0;
-                if (++lt == uv.ntiles) {
-                    lt = 0;
-                    u = next_busy(args, u + gridDim.x, total_units, uv);
+            // advance (u, lt, grp) to the next group with a chunk to multiply
+            // and prefetch it
+            grp = first_group(km, grp + 1);
+            if (grp == NCHUNK / G) {
+                lt = next_tile<MODE>(args, uv, lt + 1);
+                if (lt == uv.ntiles) {
+                    u = next_busy<MODE>(args, u + gridDim.x, total_units, uv);
+                    lt = u < total_units ? next_tile<MODE>(args, uv, 0) : 0;
+                }
+                if (u < total_units) {
+                    km = chunk_mask<MODE>(args, uv, lt);
+                    grp = first_group(km, 0);
                 }
             }
             if (u < total_units) {
@@ -394,6 +490,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
 #pragma unroll
             for (int i = 0; i < G; ++i) {
                 const int c = cur_grp * G + i;
+                if (MODE == MODE_TREE && !((cur_km >> c) & 1u)) continue;
                 const int s = (int)(g % STAGES);
                 const uint32_t r = g / STAGES;
                 if (!warp_wait(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err, lane)) goto done;
@@ -408,10 +505,11 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 }
                 store_half_chunk(stageB + (size_t)s * B_STAGE, row, hw, cu[i]);
                 tp_acc += __popc(cu[i].x) + __popc(cu[i].y);
-                if (c == NCHUNK - 1) {                 // half row complete: |t| part for the epilogue
-                    tpop_s[((tile & 1u) * 2 + hw) * TN + row] = tp_acc;
+                if (c == last_c) {                     // half row complete: |t| part for the epilogue
+                    const uint32_t tr = tile & (TP_RING - 1);
+                    tpop_s[(tr * 2 + hw) * TN + row] = tp_acc;
                     const uint32_t mn = __reduce_min_sync(0xffffffffu, tp_acc);
-                    if (lane == 0) tmin_s[((tile & 1u) * 2 + hw) * (TN / 32) + rg] = mn;
+                    if (lane == 0) tmin_s[(tr * 2 + hw) * (TN / 32) + rg] = mn;
                     tp_acc = 0;
                     ++tile;
                 }
@@ -427,13 +525,16 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
             uint32_t g = 0, t = 0;
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
                 const Unit uv = get_unit(args, u);
-                for (int64_t lt = 0; lt < uv.ntiles; ++lt, ++t) {
+                for (int64_t lt = next_tile<MODE>(args, uv, 0); lt < uv.ntiles;
+                     lt = next_tile<MODE>(args, uv, lt + 1), ++t) {
                     const uint32_t acc = t & 1u, ra = t >> 1;
                     if (!wait_or_abort(&ctl->acc_empty[acc], (ra & 1u) ^ 1u, ctl, err)) goto mma_done;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + acc * ACC_COLS;
                     const int n_qt = uv.mt[1] >= 0 ? 2 : 1;
-                    for (int c = 0; c < NCHUNK; ++c, ++g) {
+                    uint32_t km = chunk_mask<MODE>(args, uv, lt);
+                    bool first = true;
+                    for (; km; km &= km - 1, ++g) {
                         const int s = (int)(g % STAGES);
                         const uint32_t r = g / STAGES;
                         if (!wait_or_abort(&ctl->full[s], r & 1u, ctl, err)) goto mma_done;
@@ -447,9 +548,10 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                                     a_base + (uint32_t)i * A_STAGE + kk * 2 * LBO, LBO, SBO);
                                 const uint64_t bd = smem_desc_kmajor(b_base + kk * 2 * LBO, LBO, SBO);
                                 mma_e4m3(d_tmem + (uint32_t)i * TN, ad, bd, IDESC,
-                                         (c | kk) != 0 ? 1u : 0u);
+                                         (!first || kk != 0) ? 1u : 0u);
                             }
                         }
+                        first = false;
                         mma_commit(&ctl->empty[s]);
                     }
                     mma_commit(&ctl->acc_full[acc]);
@@ -477,18 +579,53 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
             const int64_t qi = uv.mt[qt] * TM + row;   // query (split mode) or pair slot (list mode)
             const bool valid = present && row < uv.nvalid[qt];
             const QueryWeights w = query_weights(valid ? args.qpop[qi] : 0u);
+            // a cap known to be >= the exact k-th key: nothing above it is kept
+            const uint32_t capk =
+                (MODE != MODE_PLAIN && args.cap && valid) ? __ldg(args.cap + qi) : 0xFFFFFFFFu;
+            const uint64_t capw = capk == 0xFFFFFFFFu ? kEmpty : pack(capk, 0xFFFFFFFFu);
             // key = A*Z + B*P = (|q| - O) Z + (|t| - O) P = |t| P + |q| Z - O (Z + P)
             const uint32_t qz = w.pop * w.Z, zp = w.Z + w.P;
             for (int j = 0; j < k; ++j) L[j] = kEmpty;
-            uint64_t worst = kEmpty;
-            uint32_t wkey = 0xFFFFFFFFu;      // key part of `worst`
-            for (int64_t lt = 0; lt < uv.ntiles; ++lt, ++t) {
+            uint64_t worst = capw;
+            uint32_t wkey = capk;             // key part of `worst`
+            for (int64_t lt = next_tile<MODE>(args, uv, 0); lt < uv.ntiles;
+                 lt = next_tile<MODE>(args, uv, lt + 1), ++t) {
                 const uint32_t acc = t & 1u, ra = t >> 1;
                 if (!warp_wait(&ctl->acc_full[acc], ra & 1u, ctl, err, lane)) goto done;
                 tc_fence_after();
                 const int64_t base = uv.r0 + lt * TN;
-                const uint32_t *tp0 = tpop_s + (t & 1u) * 2 * TN, *tp1 = tp0 + TN;
-                const uint32_t *tm0 = tmin_s + (t & 1u) * 2 * (TN / 32), *tm1 = tm0 + TN / 32;
+                if constexpr (MODE == MODE_BOUND) {
+                    // bound pass: row j of the slice is the image of scan tile
+                    // base + 32 cb + j; a bit per tile some valid query may need
+                    for (int cb = 0; cb < (present ? TN / 32 : 0); ++cb) {
+                        uint32_t v[32];
+                        tmem_ld_32x32b_x32(lane_base + acc * ACC_COLS + (uint32_t)qt * TN + cb * 32, v);
+                        tmem_ld_wait();
+                        const int64_t b0 = base + cb * 32;
+                        const int m = (int)(uv.r1 - b0 < 32 ? (uv.r1 - b0 > 0 ? uv.r1 - b0 : 0) : 32);
+                        uint32_t bits = 0;
+                        if (valid) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const uint32_t o =
+                                    __float_as_uint(fmaf(__uint_as_float(v[j]), 4096.0f, 8388608.0f)) -
+                                    0x4B000000u;
+                                const uint32_t lb = (w.pop - o) * w.Z;   // popc(q & ~image) * Z
+                                if (j < m && lb <= capk) bits |= 1u << j;
+                            }
+                        }
+                        bits = __reduce_or_sync(0xffffffffu, bits);
+                        if (lane == 0 && bits)
+                            atomicOr(args.need_out + uv.mp * args.need_words + (b0 >> 5), bits);
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
+                    continue;
+                }
+                const uint32_t tr = t & (TP_RING - 1);
+                const uint32_t *tp0 = tpop_s + tr * 2 * TN, *tp1 = tp0 + TN;
+                const uint32_t *tm0 = tmin_s + tr * 2 * (TN / 32), *tm1 = tm0 + TN / 32;
                 for (int cb = 0; cb < (present ? TN / 32 : 0); ++cb) {
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(lane_base + acc * ACC_COLS + (uint32_t)qt * TN + cb * 32, v);
@@ -520,6 +657,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                         const uint32_t key = tpj * w.P + qz - o * zp;
                         if (j < m && key <= wkey) {   // rare once the list has filled
                             worst = list_insert(L, k, key, b0 + j, args.idx_map, worst);
+                            if (MODE == MODE_TREE) worst = worst < capw ? worst : capw;
                             wkey = (uint32_t)(worst >> 32);
                         }
                     }
@@ -528,7 +666,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
             }
-            if (valid) {
+            if (MODE != MODE_BOUND && valid) {
                 uint64_t *out = args.units ? args.partial + (uv.out_base + qi) * k
                                            : args.partial + (uv.sp * nq + qi) * k;
                 for (int j = 0; j < k; ++j) out[j] = L[j];
@@ -566,7 +704,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
                     int64_t nq, int k, cudaStream_t s, Scratch &scratch, uint64_t **partial_out,
                     int *n_split_out, const TuneCfg *cfg)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel, (int)SMEM_BYTES));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN>, (int)smem_bytes(MODE_PLAIN)));
     const int n_mtiles = (int)((nq + TM - 1) / TM);
     const int n_mpairs = (n_mtiles + QT - 1) / QT;
     const int64_t n_ntiles = (n + TN - 1) / TN;
@@ -594,7 +732,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
     widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, nq, n_mtiles, a_exp, qpop);
     DT_CUDA_TRY(cudaGetLastError());
-    TcArgs a;
+    TcArgs a{};
     a.db = db;
     a.n = n;
     a.a_exp = a_exp;
@@ -611,7 +749,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.n_units = nullptr;
     a.partial = partial;
     a.err = err;
-    bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
+    bf_tc_kernel<MODE_PLAIN><<<grid, THREADS, smem_bytes(MODE_PLAIN), s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     *partial_out = partial;
     *n_split_out = n_split;
@@ -634,7 +772,7 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
                     const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
                     cudaStream_t s)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel, (int)SMEM_BYTES));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN>, (int)smem_bytes(MODE_PLAIN)));
     if (max_tiles <= 0) return DT_OK;
     unsigned char *a_exp = nullptr;
     uint32_t *qpop = nullptr, *err = nullptr;
@@ -659,7 +797,7 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.partial = partial;
     a.err = err;
     const int grid = (int)std::min<int64_t>(max_tiles, sm_count());   // units <= tiles
-    bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
+    bf_tc_kernel<MODE_PLAIN><<<grid, THREADS, smem_bytes(MODE_PLAIN), s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
@@ -682,7 +820,7 @@ int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
                         const int64_t *n_units, int64_t max_units, int k, uint64_t *partial,
                         cudaStream_t s)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel, (int)SMEM_BYTES));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN>, (int)smem_bytes(MODE_PLAIN)));
     if (max_units <= 0) return DT_OK;
     uint32_t *err = nullptr;
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
@@ -699,8 +837,98 @@ int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
     a.partial = partial;
     a.err = err;
     const int grid = (int)std::min<int64_t>(max_units, sm_count());
-    bf_tc_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(a);
+    bf_tc_kernel<MODE_PLAIN><<<grid, THREADS, smem_bytes(MODE_PLAIN), s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
+    return DT_OK;
+}
+
+int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int32_t *slot_q,
+                   const uint32_t *cap_slot, int n_mtiles, int k, Scratch &scratch, cudaStream_t s,
+                   uint64_t **partial_out, int *n_split_out, std::vector<uint32_t> *need_host,
+                   int64_t *need_words_out)
+{
+    static_assert(TN == kScanTileRows, "scan tiles are tensor-core tiles");
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_BOUND>, (int)smem_bytes(MODE_BOUND)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_TREE>, (int)smem_bytes(MODE_TREE)));
+    const int64_t n = ix->n;
+    const int64_t n_tt = (n + TN - 1) / TN;             // scan tiles
+    const int64_t need_words = (n_tt + 31) / 32;
+    const int n_mpairs = (n_mtiles + QT - 1) / QT;
+    const int sms = sm_count();
+    unsigned char *a_exp = nullptr;
+    uint32_t *qpop = nullptr, *need = nullptr, *err = nullptr;
+    uint64_t *partial = nullptr;
+    DT_CUDA_TRY(scratch.alloc(&a_exp, (size_t)n_mtiles * NCHUNK * A_STAGE));
+    DT_CUDA_TRY(scratch.alloc(&qpop, (size_t)n_mtiles * TM * 4));
+    DT_CUDA_TRY(scratch.alloc(&need, (size_t)n_mpairs * need_words * 4));
+    DT_CUDA_TRY(cudaMemsetAsync(need, 0, (size_t)n_mpairs * need_words * 4, s));
+    DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
+    const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
+    widen_gather_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, slot_q, nullptr, n_mtiles,
+                                                                        a_exp, qpop);
+    DT_CUDA_TRY(cudaGetLastError());
+
+    // pass 1: every (pair of slot tiles, tile image) bound; the images are
+    // the rows of a small database of n_tt rows
+    TcArgs b{};
+    b.db = ix->tile_or;
+    b.n = n_tt;
+    b.a_exp = a_exp;
+    b.qpop = qpop;
+    b.nq = nq;
+    b.k = k;
+    b.n_mtiles = n_mtiles;
+    b.n_mpairs = n_mpairs;
+    b.n_ntiles = (n_tt + TN - 1) / TN;
+    {
+        const int splits = pick_bf_splits(n_mpairs, b.n_ntiles, sms);
+        b.tiles_per_split = (b.n_ntiles + splits - 1) / splits;
+        b.n_split = (int)((b.n_ntiles + b.tiles_per_split - 1) / b.tiles_per_split);
+    }
+    b.cap = cap_slot;
+    b.need_out = need;
+    b.need_words = need_words;
+    b.err = err;
+    bf_tc_kernel<MODE_BOUND><<<(int)std::min<int64_t>((int64_t)n_mpairs * b.n_split, sms), THREADS,
+                               smem_bytes(MODE_BOUND), s>>>(b);
+    DT_CUDA_TRY(cudaGetLastError());
+
+    // pass 2: the needed scan tiles of each pair, zero K chunks skipped
+    TcArgs a{};
+    a.db = ix->db_tree;
+    a.n = n;
+    a.a_exp = a_exp;
+    a.qpop = qpop;
+    a.idx_map = ix->perm;
+    a.nq = nq;
+    a.k = k;
+    a.n_mtiles = n_mtiles;
+    a.n_mpairs = n_mpairs;
+    a.n_ntiles = n_tt;
+    TuneCfg c{0, 0};
+    tune_lookup(TUNE_TREE_TC, n, nq, k, &c);
+    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_tt) : pick_bf_splits(n_mpairs, n_tt, sms);
+    a.tiles_per_split = (n_tt + splits - 1) / splits;
+    a.n_split = (int)((n_tt + a.tiles_per_split - 1) / a.tiles_per_split);
+    a.need = need;
+    a.need_words = need_words;
+    a.kmask = ix->tile_kmask;
+    a.cap = cap_slot;
+    a.err = err;
+    DT_CUDA_TRY(scratch.alloc(&partial, (size_t)a.n_split * nq * k * 8));
+    DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)a.n_split * nq * k * 8, s));
+    a.partial = partial;
+    bf_tc_kernel<MODE_TREE><<<(int)std::min<int64_t>((int64_t)n_mpairs * a.n_split, sms), THREADS,
+                              smem_bytes(MODE_TREE), s>>>(a);
+    DT_CUDA_TRY(cudaGetLastError());
+    if (need_host) {
+        need_host->resize((size_t)n_mpairs * need_words);
+        DT_CUDA_TRY(cudaMemcpyAsync(need_host->data(), need, need_host->size() * 4,
+                                    cudaMemcpyDeviceToHost, s));
+    }
+    *partial_out = partial;
+    *n_split_out = a.n_split;
+    *need_words_out = need_words;
     return DT_OK;
 }
 

@@ -670,7 +670,56 @@ int build_tree(const uint64_t *db, int64_t n, int leaf_size, int use_and, int fu
     DT_CUDA_TRY(cudaMemcpyAsync(ix->perm, perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     invert_kernel<<<std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(perm, n, ix->iperm);
     DT_CUDA_TRY(cudaGetLastError());
+    if (int rc = make_tile_images(ix->db_tree, n, &ix->tile_or, &ix->tile_kmask, s)) return rc;
     DT_CUDA_TRY(cudaStreamSynchronize(s));
+    return DT_OK;
+}
+
+// Tile images: a warp per run of kScanTileRows tree-ordered rows; lane l
+// owns the 128-bit chunk l (words 2l, 2l + 1) of the running OR, so the
+// chunk mask is one ballot.
+__global__ void tile_images_kernel(const uint64_t *__restrict__ db_tree, int64_t n, int64_t n_tt,
+                                   uint64_t *__restrict__ tile_or, uint32_t *__restrict__ kmask)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (; t < n_tt; t += stride) {
+        const int64_t r0 = t * kScanTileRows, r1 = min(n, r0 + kScanTileRows);
+        uint4 o = make_uint4(0u, 0u, 0u, 0u);
+        for (int64_t r = r0; r < r1; ++r) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(db_tree + r * kWords) + lane);
+            o.x |= v.x; o.y |= v.y; o.z |= v.z; o.w |= v.w;
+        }
+        reinterpret_cast<uint4 *>(tile_or + t * kWords)[lane] = o;
+        const uint32_t m = __ballot_sync(0xffffffffu, (o.x | o.y | o.z | o.w) != 0u);
+        if (lane == 0) kmask[t] = m;
+    }
+}
+
+int make_tile_images(const uint64_t *db_tree, int64_t n, uint64_t **tile_or, uint32_t **kmask,
+                     cudaStream_t s)
+{
+    *tile_or = nullptr;
+    *kmask = nullptr;
+    const int64_t n_tt = (n + kScanTileRows - 1) / kScanTileRows;
+    uint64_t *o = nullptr;
+    uint32_t *m = nullptr;
+    cudaError_t e = cudaMalloc((void **)&o, (size_t)n_tt * kWords * 8);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&m, (size_t)n_tt * 4);
+    if (e == cudaSuccess) {
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((n_tt + 7) / 8, (int64_t)sm_count() * 16));
+        tile_images_kernel<<<(unsigned)blocks, 256, 0, s>>>(db_tree, n, n_tt, o, m);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        cudaFree(o);
+        cudaFree(m);
+        set_error(std::string("make_tile_images: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? DT_ENOMEM : DT_ECUDA;
+    }
+    *tile_or = o;
+    *kmask = m;
     return DT_OK;
 }
 
@@ -686,6 +735,7 @@ int fill_index_rows(const uint64_t *db, dt_index *ix, cudaStream_t s)
                                                                                    ix->db_tree);
     invert_kernel<<<std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(ix->perm, n, ix->iperm);
     DT_CUDA_TRY(cudaGetLastError());
+    if (int rc = make_tile_images(ix->db_tree, n, &ix->tile_or, &ix->tile_kmask, s)) return rc;
     DT_CUDA_TRY(cudaStreamSynchronize(s));
     return DT_OK;
 }

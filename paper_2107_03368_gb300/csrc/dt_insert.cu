@@ -395,6 +395,14 @@ int insert_tree(dt_index *ix, const uint64_t *d_new, int64_t m, cudaStream_t s)
     invert_u32_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, s>>>(
         perm_new.as<uint32_t>(), n, iperm_new.as<uint32_t>());
     DT_CUDA_TRY(cudaGetLastError());
+    Owned tor_new, tmask_new;
+    {
+        uint64_t *to = nullptr;
+        uint32_t *tm = nullptr;
+        if ((rc = make_tile_images(db_new.as<uint64_t>(), n, &to, &tm, s)) != DT_OK) return rc;
+        tor_new.p = to;
+        tmask_new.p = tm;
+    }
     DT_CUDA_TRY(cudaStreamSynchronize(s));
 
     cudaFree(ix->db_tree);
@@ -403,6 +411,10 @@ int insert_tree(dt_index *ix, const uint64_t *d_new, int64_t m, cudaStream_t s)
     cudaFree(ix->node);
     cudaFree(ix->or_img);
     cudaFree(ix->and_img);
+    cudaFree(ix->tile_or);
+    cudaFree(ix->tile_kmask);
+    ix->tile_or = static_cast<uint64_t *>(tor_new.release());
+    ix->tile_kmask = static_cast<uint32_t *>(tmask_new.release());
     ix->db_tree = static_cast<uint64_t *>(db_new.release());
     ix->perm = static_cast<uint32_t *>(perm_new.release());
     ix->iperm = static_cast<uint32_t *>(iperm_new.release());

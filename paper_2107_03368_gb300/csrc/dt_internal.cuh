@@ -128,7 +128,8 @@ void set_error(const std::string &msg);
 
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Every scratch allocation of the library: cudaMallocAsync, except that a
+// Every scratch allocation of the library: stream-ordered, from the
+// library's own pool (graph memory under stream capture), except that a
 // test hook (dt_debug_fail_allocation) can make the n-th one report
 // cudaErrorMemoryAllocation.
 cudaError_t dt_malloc_async(void **p, size_t bytes, cudaStream_t s);
@@ -158,7 +159,7 @@ class Scratch {
     }
 
   private:
-    static constexpr int kMax = 16;
+    static constexpr int kMax = 32;
     cudaStream_t s_;
     void *p_[kMax] = {};
     int n_ = 0;
@@ -222,13 +223,19 @@ struct dt_index {
     uint64_t *or_img = nullptr;     // [n_nodes][64]
     uint64_t *and_img = nullptr;    // [n_nodes][64] when use_and
     dtk::NodeRec *node = nullptr;   // [n_nodes]
+    // Scan tiles of the batched search: tile i = tree positions
+    // [128 i, 128 i + 128).  tile_or[i] is the OR image of its rows and
+    // tile_kmask[i] has bit c set when that image has a bit in the 128-bit
+    // chunk c (words 2c, 2c + 1).  ceil(n / 128) entries each.
+    uint64_t *tile_or = nullptr;
+    uint32_t *tile_kmask = nullptr;
 };
 
 namespace dtk {
 // Autotuner table (autotune.cu): a launch shape per kernel kind and problem size.
-enum TuneKind { TUNE_TREE = 0, TUNE_POPC = 1, TUNE_TC = 2 };
+enum TuneKind { TUNE_TREE = 0, TUNE_POPC = 1, TUNE_TC = 2, TUNE_TREE_TC = 3 };
 struct TuneCfg {
-    int a;   // TREE: threads per block; POPC / TC: database splits
+    int a;   // TREE: threads per block; POPC / TC / TREE_TC: database splits
     int b;   // TREE: resident blocks per SM
 };
 bool tune_lookup(TuneKind kind, int64_t n, int64_t nq, int k, TuneCfg *cfg);
@@ -273,6 +280,30 @@ int grow_forest(const uint64_t *db, uint32_t *perm, int64_t n_rows, const std::v
                 std::vector<NodeRec> &recs, int64_t *n_leaves, int32_t *depth);
 int insert_tree(dt_index *ix, const uint64_t *d_new, int64_t m, cudaStream_t s);
 int fill_index_rows(const uint64_t *db, dt_index *ix, cudaStream_t s);
+// Rows of a scan tile of the batched tree search (= the tensor-core tile N).
+constexpr int kScanTileRows = 128;
+// Tile images of n tree-ordered rows: *tile_or [ceil(n/128)][64] and
+// *kmask [ceil(n/128)], both cudaMalloc'ed here (the caller owns them).
+int make_tile_images(const uint64_t *db_tree, int64_t n, uint64_t **tile_or, uint32_t **kmask,
+                     cudaStream_t s);
+// Batched tree search (dt_search.cu): all queries' descents, then the
+// tile-level bound pass and scan on the tensor cores.
+int launch_dt_search_batched(const dt_index *ix, const uint64_t *q, int64_t nq, int k,
+                             const uint32_t *seeds, int n_seed, uint32_t *idx, float *score,
+                             uint16_t *ab, dt_stats *stats, cudaStream_t s);
+// The tensor-core passes of the batched tree search (bf_tc.cu).  Queries
+// sit in slots (slot i < nq holds query slot_q[i]; slot_q has
+// n_mtiles * 128 entries, -1 past nq), each with a key cap cap_slot[slot]
+// that is >= its exact k-th result's key (0xFFFFFFFF: none).  Pass 1 bounds
+// every (pair of 128-slot tiles, scan tile) by the tile images and marks
+// the scan tiles some query of the pair may need; pass 2 scans those
+// tiles, skipping K chunks the tile has no bit in, into per-split sorted
+// lists partial[split][slot][k] of (key, original index).  *need (host
+// copy, n_mpairs x need_words words) is filled when need_host is non-null.
+int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int32_t *slot_q,
+                   const uint32_t *cap_slot, int n_mtiles, int k, Scratch &scratch, cudaStream_t s,
+                   uint64_t **partial_out, int *n_split_out, std::vector<uint32_t> *need_host,
+                   int64_t *need_words_out);
 int launch_quicci(const float *d_vertices, int64_t n_vertices, const int32_t *d_triangles,
                   int64_t n_triangles, const float *d_points, const float *d_normals,
                   int64_t n_points, float support_radius, int modified, uint64_t *d_out,

@@ -84,6 +84,7 @@ def load():
             "dt_export": ([P, P, P, P, P, P, P, P], ctypes.c_int),
             "dt_search": ([P, P, i64, i32, P, P, P, P, P], ctypes.c_int),
             "dt_search_seeded": ([P, P, i64, i32, P, i32, P, P, P, P, P], ctypes.c_int),
+            "dt_search_path": ([P, P, i64, i32, P, i32, P, P, P, P, i32, P], ctypes.c_int),
             "bf_search": ([P, i64, P, i64, i32, P, P, P, i32, P], ctypes.c_int),
             "bf_search_noalloc": ([P, i64, P, i64, i32, P, P, P, P], ctypes.c_int),
             "retrieve_objects": ([P, P, i32, P, P, i32, i64, i32, u64, P, P, P, i32, P],
@@ -268,6 +269,27 @@ def dt_search_seeded(index: Index, q, k, seeds, with_ab=False, stats=False, out=
                                    seeds.shape[1], _ptr(idx), _ptr(score), _ptr(ab),
                                    ctypes.byref(st) if st is not None else None,
                                    _stream(stream)), "dt_search_seeded")
+    return idx, score, ab, (st.as_dict() if st is not None else None)
+
+
+def dt_search_path(index: Index, q, k, path, seeds=None, with_ab=False, stats=False, out=None,
+                   stream=None):
+    """dt_search (seeds None) or dt_search_seeded with the traversal forced:
+    path 0 automatic, 1 per query, 2 batched.  Same results on every path."""
+    q = _desc(q, "q")
+    n_seed = 0
+    if seeds is not None:
+        if seeds.dim() != 2 or seeds.shape[0] != q.shape[0]:
+            raise ValueError("seeds must be [nq, n_seed]")
+        if seeds.dtype not in (torch.int32, torch.uint32) or not seeds.is_contiguous():
+            raise ValueError("seeds must be a contiguous int32 tensor")
+        n_seed = seeds.shape[1]
+    idx, score, ab = _outputs(q.shape[0], k, q.device, with_ab, out)
+    st = Stats() if stats else None
+    _check(load().dt_search_path(index.handle, _ptr(q), q.shape[0], k,
+                                 _ptr(seeds) if n_seed else None, n_seed, _ptr(idx), _ptr(score),
+                                 _ptr(ab), ctypes.byref(st) if st is not None else None, path,
+                                 _stream(stream)), "dt_search_path")
     return idx, score, ab, (st.as_dict() if st is not None else None)
 
 

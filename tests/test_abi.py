@@ -71,6 +71,9 @@ def test_new_entry_points_check_their_arguments_first():
     assert lib.dt_search_seeded(dummy, None, 5, 1, None, 5000, None, None, None, None,
                                 None) == dt.DT_EINVAL
     assert "n_seed" in dt.dt_last_error()
+    assert dt.load().dt_search_path(dummy, None, 5, 1, None, 0, None, None, None, None, 3,
+                                    None) == dt.DT_EINVAL
+    assert "path" in dt.dt_last_error()
     assert lib.ivf_search(None, None, None, 5, 1, 1, None, None, None, 0, None) == dt.DT_EINVAL
     assert lib.enc_embed(None, None, 5, None, None, 0, None) == dt.DT_EINVAL
     assert dt.load().dt_insert(None, None, 5, None) == dt.DT_EINVAL

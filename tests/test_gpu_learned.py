@@ -129,14 +129,16 @@ def test_learned_proposal_gains_over_plain_tree_search():
     128 probed lists it finds the exact nearest neighbour for >= 95% of
     queries while scanning under half the descriptors the exact tree search
     scans; its answers, used as a warm start, leave the tree search exact
-    and scanning fewer descriptors."""
+    and scanning fewer descriptors (per-query traversal; the batched one
+    shares scans among 256 queries and is checked in test_gpu_tree.py)."""
     db, _ = synth.database(31, 40_000, per_object=500, pool=20)
     d_db = to_dev(db)
     q, _ = synth.queries(32, db, 2000)
     d_q = to_dev(q)
     exact = dt.bf_search(d_db, d_q, 1)[0][:, 0]
     ix = dt.dt_build(d_db)
-    _, _, _, plain1 = dt.dt_search(ix, d_q, 1, stats=True)
+    # work is compared on the per-query traversal, whose counts are per query
+    _, _, _, plain1 = dt.dt_search_path(ix, d_q, 1, 1, stats=True)
 
     enc = learned.Encoder(seed=9)
     learned.train(enc, d_db, lambda r: synth.queries(3000 + r, db, 4096)[0], steps=300,
@@ -152,8 +154,9 @@ def test_learned_proposal_gains_over_plain_tree_search():
     assert per_q < 0.5 * tree_per_q
 
     seeds, _, _ = ivf.search(d_q, 10, n_probe=2)
-    _, _, _, plain = dt.dt_search(ix, d_q, 10, stats=True)
-    idx, score, ab, warm = dt.dt_search_seeded(ix, d_q, 10, seeds, with_ab=True, stats=True)
+    _, _, _, plain = dt.dt_search_path(ix, d_q, 10, 1, stats=True)
+    idx, score, ab, warm = dt.dt_search_path(ix, d_q, 10, 1, seeds=seeds, with_ab=True,
+                                             stats=True)
     from helpers import assert_matches_oracle
     assert_matches_oracle(db, q, 10, idx, score, ab)
     assert warm["descs_scanned"] < plain["descs_scanned"]
