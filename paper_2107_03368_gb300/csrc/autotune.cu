@@ -6,7 +6,9 @@
 //          flight at once);
 //   POPC   popcount brute force: number of database splits (grid depth);
 //   TC     tensor-core brute force: number of database splits (work units
-//          per persistent CTA).
+//          per persistent CTA), and whether the database is widened inside
+//          the kernel or once beforehand (b = 1 / 2);
+//   TREE_TC  the batched tree search's scan: the same two knobs.
 // dt_autotune times each candidate on the caller's data with CUDA events
 // and keeps the fastest per key (kind, log2 n, log2 nq, k, SM count) in a
 // process-wide table; launchers look the key up and fall back to their
@@ -193,7 +195,7 @@ int dt_tune_load(const char *path)
     std::lock_guard<std::mutex> lock(g_tune_mu);
     int kind, nl, ql, k, sms, a, b, loaded = 0;
     while (std::fscanf(f, "%d %d %d %d %d %d %d", &kind, &nl, &ql, &k, &sms, &a, &b) == 7) {
-        if (kind < TUNE_TREE || kind > TUNE_TC || a <= 0 || b < 0) continue;
+        if (kind < TUNE_TREE || kind > TUNE_TREE_TC || a <= 0 || b < 0) continue;
         g_tune[Key(kind, nl, ql, k, sms)] = TuneCfg{a, b};
         ++loaded;
     }

@@ -57,8 +57,14 @@ constexpr int STAGE = QT * A_STAGE + B_STAGE;   // 48 KB
 constexpr uint32_t LBO = 128;           // next core matrix along K
 constexpr uint32_t SBO = (KC / 16) * 128;  // next 8-row group (1024 B)
 constexpr int EPI_WARPS = 8, PROD_WARPS = 8;    // producers: two per database row
-constexpr int MMA_WARP = EPI_WARPS + PROD_WARPS;
-constexpr int THREADS = (MMA_WARP + 1) * 32;
+// Warp roles.  In-kernel widening: epilogue 0-7, producers 8-15, MMA 16.
+// Pre-widened database (PRE): epilogue 0-15, copy issuer 16, MMA 17; each
+// epilogue warp then covers half of its tile's columns, so a query ends a
+// unit with one sorted list per half.
+__host__ __device__ constexpr int epi_warps(bool pre) { return pre ? 2 * EPI_WARPS : EPI_WARPS; }
+__host__ __device__ constexpr int mma_warp(bool pre) { return pre ? 17 : 16; }
+__host__ __device__ constexpr int kernel_threads(bool pre) { return (mma_warp(pre) + 1) * 32; }
+__host__ __device__ constexpr int lists_per_unit(bool pre) { return pre ? 2 : 1; }
 constexpr uint32_t ACC_COLS = QT * TN;  // one accumulator: 128 columns per query tile
 constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;    // double-buffered: 512
 constexpr uint32_t IDESC = idesc_e4m3_f32(TM, TN);
@@ -91,11 +97,17 @@ enum { MODE_PLAIN = 0, MODE_TREE = 1, MODE_BOUND = 2 };
 // STAGES + 2 entries are in use at most.
 __host__ __device__ constexpr int tp_ring(int mode) { return mode == MODE_TREE ? 8 : 2; }
 static_assert(tp_ring(MODE_TREE) >= STAGES + 2, "|t| ring of the tree mode");
-// + |t| halves [ring][2 halves][TN] and their 32-row minima [ring][2][TN / 32]
+// One ring entry per tile, contiguous so that a single bulk copy can fill
+// it: |t| of every row as two half-row sums [2][TN], then the smallest half
+// sum of each 32 rows [2][TN / 32] (uint32 throughout).  The pre-widened
+// database keeps one such record per tile (whole |t| in the first half,
+// zeros in the second).
+constexpr int SIDE_WORDS = 2 * TN + 2 * (TN / 32);
+constexpr uint32_t SIDE_BYTES = SIDE_WORDS * 4;          // 1,056
+static_assert(SIDE_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
 __host__ __device__ constexpr size_t smem_bytes(int mode)
 {
-    return STAGE_BYTES + sizeof(TcCtl) + (size_t)tp_ring(mode) * 2 * TN * 4 +
-           (size_t)tp_ring(mode) * 2 * (TN / 32) * 4 + 1024;
+    return STAGE_BYTES + sizeof(TcCtl) + (size_t)tp_ring(mode) * SIDE_BYTES + 1024;
 }
 
 __device__ uint32_t g_tc_error;  // a bounded wait gave up (DT_ETIMEOUT)
@@ -204,6 +216,25 @@ __global__ void widen_gather_kernel(const uint64_t *__restrict__ q, const int32_
     }
 }
 
+// |t| records of pre-widened database tiles (one CTA of TN threads per
+// tile) from the per-row |t|; rows past n count 0.
+__global__ void side_kernel(const uint32_t *__restrict__ rowpop, int64_t n,
+                            uint32_t *__restrict__ side)
+{
+    const int64_t t = blockIdx.x;
+    const int row = threadIdx.x, lane = row & 31, w = row >> 5;
+    const int64_t i = t * TN + row;
+    const uint32_t v = i < n ? rowpop[i] : 0u;
+    uint32_t *e = side + t * SIDE_WORDS;
+    e[row] = v;
+    e[TN + row] = 0u;
+    const uint32_t mn = __reduce_min_sync(0xffffffffu, v);
+    if (lane == 0) {
+        e[2 * TN + w] = mn;
+        e[2 * TN + TN / 32 + w] = 0u;
+    }
+}
+
 // Bounded wait that also gives up when another role aborted.  The thread
 // sleeps inside try_wait (up to 0.5 us per poll) instead of spinning, so
 // waiting warps leave the issue slots to the working ones.
@@ -255,16 +286,19 @@ struct TcArgs {
     //             tile: the others contribute nothing and are skipped
     //   cap       per query row, a key >= its exact k-th result's key: larger
     //             keys are not kept, and in bound mode it is the threshold
-    //   mode      0 = top-k lists; 1 = bound pass: the "database" rows are
-    //             tile images, row g's bound popc(q & ~image) * Z is compared
-    //             with the cap and need_out bit (mp, g) is set if some query
-    //             of the pair may need scan tile g
+    //   need_out  bound pass (MODE_BOUND): the "database" rows are tile
+    //             images; bit (mp, g) is set when row g's bound
+    //             popc(q & ~image) * Z is <= the cap of some query of pair mp
     const uint32_t *need;
     int64_t need_words;
     const uint32_t *kmask;
     const uint32_t *cap;
     uint32_t *need_out;
-    int mode;
+    // Pre-widened database (split mode, PRE kernels): stage images
+    // b_exp[tile][chunk][B_STAGE] of global tile `tile` (rows 128 tile ..),
+    // and per tile its |t| record b_side[tile][SIDE_WORDS].
+    const unsigned char *b_exp;
+    const uint32_t *b_side;
 };
 
 // One work unit: query tiles mt[0], mt[1] (mt[1] < 0: absent) against
@@ -387,8 +421,8 @@ __device__ __noinline__ uint64_t list_insert(uint64_t *L, int k, uint32_t key, i
     return L[k - 1];
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
+template <int MODE, bool PRE>
+__global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcArgs args)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -396,22 +430,23 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
     unsigned char *stageA = smem;                                   // [STAGES][QT][A_STAGE]
     unsigned char *stageB = smem + (size_t)STAGES * QT * A_STAGE;   // [STAGES][B_STAGE]
     TcCtl *ctl = reinterpret_cast<TcCtl *>(smem + STAGE_BYTES);
-    // |t| of each row as two half-row sums [tile % TP_RING][half][TN], and
-    // the smallest half sum of each 32 rows [tile % TP_RING][half][TN / 32]
-    uint32_t *tpop_s = reinterpret_cast<uint32_t *>(smem + STAGE_BYTES + sizeof(TcCtl));
+    // |t| ring: entry tile % TP_RING (SIDE_WORDS words, layout above)
+    static_assert(sizeof(TcCtl) % 16 == 0, "ring entries start 16-byte aligned");
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smem + STAGE_BYTES + sizeof(TcCtl));
     constexpr int TP_RING = tp_ring(MODE);
-    uint32_t *tmin_s = tpop_s + TP_RING * 2 * TN;
     uint32_t *err = args.err;
 
+    constexpr int EPI = epi_warps(PRE), MMAW = mma_warp(PRE), NL = lists_per_unit(PRE);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&ctl->full[s], 1 + PROD_WARPS);   // A bytes + one arrival per producer warp
+            // A (and with PRE, B) bytes + one arrival per producer warp
+            mbar_init(&ctl->full[s], PRE ? 1 : 1 + PROD_WARPS);
             mbar_init(&ctl->empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&ctl->acc_full[a], 1);
-            mbar_init(&ctl->acc_empty[a], EPI_WARPS);
+            mbar_init(&ctl->acc_empty[a], EPI);
         }
         mbar_init(&ctl->final_bar, 1);
         ctl->abort = 0u;
@@ -428,7 +463,49 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
 
     const int64_t total_units = unit_count(args);
 
-    if (warp >= EPI_WARPS && warp < MMA_WARP) {
+    if (PRE && warp == EPI) {
+        // ------------------------------------------------ copy issuer (PRE)
+        // The database arrives widened: one thread issues, per chunk, the
+        // query tiles' chunks and the database tile's chunk, and with a
+        // tile's last chunk the tile's |t| record into the ring (at the same
+        // point of the sequence where the producers below write it).
+        if (lane == 0) {
+            uint32_t g = 0, tile = 0;
+            for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
+                const Unit uv = get_unit(args, u);
+                const int64_t mt0 = uv.mt[0], mt1 = uv.mt[1];
+                for (int64_t lt = next_tile<MODE>(args, uv, 0); lt < uv.ntiles;
+                     lt = next_tile<MODE>(args, uv, lt + 1)) {
+                    const int64_t gt = uv.t0 + lt;
+                    const uint32_t km = chunk_mask<MODE>(args, uv, lt);
+                    const int last_c = 31 - __clz(km);
+                    for (uint32_t m = km; m; m &= m - 1, ++g) {
+                        const int c = __ffs(m) - 1;
+                        const int s = (int)(g % STAGES);
+                        const uint32_t r = g / STAGES;
+                        if (!wait_or_abort(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err)) goto done;
+                        const uint32_t bytes = (mt1 >= 0 ? 2u : 1u) * A_STAGE + B_STAGE +
+                                               (c == last_c ? SIDE_BYTES : 0u);
+                        mbar_arrive_expect_tx(&ctl->full[s], bytes);
+                        unsigned char *a_dst = stageA + (size_t)s * QT * A_STAGE;
+                        bulk_g2s(a_dst, args.a_exp + ((size_t)mt0 * NCHUNK + c) * A_STAGE,
+                                 (uint32_t)A_STAGE, &ctl->full[s]);
+                        if (mt1 >= 0)
+                            bulk_g2s(a_dst + A_STAGE, args.a_exp + ((size_t)mt1 * NCHUNK + c) * A_STAGE,
+                                     (uint32_t)A_STAGE, &ctl->full[s]);
+                        bulk_g2s(stageB + (size_t)s * B_STAGE,
+                                 args.b_exp + ((size_t)gt * NCHUNK + c) * B_STAGE, (uint32_t)B_STAGE,
+                                 &ctl->full[s]);
+                        if (c == last_c) {
+                            bulk_g2s(ring + (tile & (TP_RING - 1)) * SIDE_WORDS,
+                                     args.b_side + (size_t)gt * SIDE_WORDS, SIDE_BYTES, &ctl->full[s]);
+                            ++tile;
+                        }
+                    }
+                }
+            }
+        }
+    } else if (!PRE && warp >= EPI_WARPS && warp < EPI_WARPS + PROD_WARPS) {
         // ------------------------------------------------ producers
         // Half a database row per thread (warps 8-11 the first 8 bytes of each
         // chunk, warps 12-15 the second).  Chunks are visited in groups of
@@ -507,9 +584,10 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 tp_acc += __popc(cu[i].x) + __popc(cu[i].y);
                 if (c == last_c) {                     // half row complete: |t| part for the epilogue
                     const uint32_t tr = tile & (TP_RING - 1);
-                    tpop_s[(tr * 2 + hw) * TN + row] = tp_acc;
+                    uint32_t *e = ring + tr * SIDE_WORDS;
+                    e[hw * TN + row] = tp_acc;
                     const uint32_t mn = __reduce_min_sync(0xffffffffu, tp_acc);
-                    if (lane == 0) tmin_s[(tr * 2 + hw) * (TN / 32) + rg] = mn;
+                    if (lane == 0) e[2 * TN + hw * (TN / 32) + rg] = mn;
                     tp_acc = 0;
                     ++tile;
                 }
@@ -519,7 +597,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 ++g;
             }
         }
-    } else if (warp == MMA_WARP) {
+    } else if (warp == MMAW) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             uint32_t g = 0, t = 0;
@@ -563,10 +641,12 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
         }
         __syncwarp();
     } else {
-        // ------------------------------------------------ epilogue (warps 0-7)
+        // ------------------------------------------------ epilogue (warps 0 .. EPI-1)
         // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its sub-partition) of
-        // query tile w / 4 (that tile's 128 accumulator columns).
-        const int quarter = warp & 3, qt = warp >> 2;
+        // query tile (w / 4) % 2: all of that tile's 128 accumulator columns,
+        // or with PRE the half w / 8 of them (slices cb0 .. cb1 - 1).
+        const int quarter = warp & 3, qt = (warp >> 2) & 1, half = NL > 1 ? warp >> 3 : 0;
+        const int cb0 = half * (TN / 32 / NL), cb1 = cb0 + TN / 32 / NL;
         const int row = quarter * 32 + lane;         // TMEM lane = query row of the tile
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         const int k = args.k;
@@ -597,7 +677,7 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 if constexpr (MODE == MODE_BOUND) {
                     // bound pass: row j of the slice is the image of scan tile
                     // base + 32 cb + j; a bit per tile some valid query may need
-                    for (int cb = 0; cb < (present ? TN / 32 : 0); ++cb) {
+                    for (int cb = cb0; cb < (present ? cb1 : cb0); ++cb) {
                         uint32_t v[32];
                         tmem_ld_32x32b_x32(lane_base + acc * ACC_COLS + (uint32_t)qt * TN + cb * 32, v);
                         tmem_ld_wait();
@@ -624,9 +704,9 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                     continue;
                 }
                 const uint32_t tr = t & (TP_RING - 1);
-                const uint32_t *tp0 = tpop_s + tr * 2 * TN, *tp1 = tp0 + TN;
-                const uint32_t *tm0 = tmin_s + tr * 2 * (TN / 32), *tm1 = tm0 + TN / 32;
-                for (int cb = 0; cb < (present ? TN / 32 : 0); ++cb) {
+                const uint32_t *tp0 = ring + tr * SIDE_WORDS, *tp1 = tp0 + TN;
+                const uint32_t *tm0 = tp0 + 2 * TN, *tm1 = tm0 + TN / 32;
+                for (int cb = cb0; cb < (present ? cb1 : cb0); ++cb) {
                     uint32_t v[32];
                     tmem_ld_32x32b_x32(lane_base + acc * ACC_COLS + (uint32_t)qt * TN + cb * 32, v);
                     tmem_ld_wait();
@@ -667,8 +747,9 @@ __global__ void __launch_bounds__(THREADS, 1) bf_tc_kernel(const TcArgs args)
                 if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
             }
             if (MODE != MODE_BOUND && valid) {
+                // (PRE kernels run in split mode only)
                 uint64_t *out = args.units ? args.partial + (uv.out_base + qi) * k
-                                           : args.partial + (uv.sp * nq + qi) * k;
+                                           : args.partial + ((uv.sp * NL + half) * nq + qi) * k;
                 for (int j = 0; j < k; ++j) out[j] = L[j];
             }
         }
@@ -698,13 +779,52 @@ __global__ void merge_top1_kernel(const uint64_t *__restrict__ partial, int n_sp
     if (lane == 0) nn[q] = best == kEmpty ? 0xFFFFFFFFu : (uint32_t)best;
 }
 
+// Should a split-mode scan of n rows by nq queries read a pre-widened copy
+// of the rows (kernel variant PRE)?  The copy costs one pass writing
+// n * 4 KB (8x the rows) and that much scratch; it spares every unit the
+// producers' widening.  forced: 1 never, 2 always, 0 from eight query
+// tiles on when the copy fits in half the free device memory.
+bool want_prewiden(int64_t n, int64_t nq, int forced)
+{
+    if (forced == 1) return false;
+    if (forced == 2) return true;
+    if (nq < 8 * TM) return false;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t bytes = (size_t)((n + TN - 1) / TN) * ((size_t)NCHUNK * B_STAGE + SIDE_BYTES);
+    return bytes <= free_b / 2;
+}
+
+// Stage images and |t| records of rows [0, n) of db, tiled by TN rows
+// (rows past n are zero), from `scratch`.
+int prewiden_rows(const uint64_t *db, int64_t n, Scratch &scratch, cudaStream_t s,
+                  unsigned char **b_exp, uint32_t **b_side)
+{
+    const int64_t n_tiles = (n + TN - 1) / TN;
+    uint32_t *rowpop = nullptr;
+    DT_CUDA_TRY(scratch.alloc(b_exp, (size_t)n_tiles * NCHUNK * B_STAGE));
+    DT_CUDA_TRY(scratch.alloc(b_side, (size_t)n_tiles * SIDE_BYTES));
+    DT_CUDA_TRY(scratch.alloc(&rowpop, (size_t)n_tiles * TN * 4));
+    static_assert(TN == TM && B_STAGE == A_STAGE, "database tiles widen like query tiles");
+    const int64_t items = n_tiles * TN * NCHUNK;
+    widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(db, n, (int)n_tiles, *b_exp,
+                                                                         rowpop);
+    side_kernel<<<(unsigned)n_tiles, TN, 0, s>>>(rowpop, n, *b_side);
+    DT_CUDA_TRY(cudaGetLastError());
+    return DT_OK;
+}
+
 // Per-split top-k lists of every query over db (rows reported through
 // idx_map when given).  *partial is allocated on the stream; the caller frees it.
 int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
                     int64_t nq, int k, cudaStream_t s, Scratch &scratch, uint64_t **partial_out,
                     int *n_split_out, const TuneCfg *cfg)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, true>, (int)smem_bytes(MODE_PLAIN)));
     const int n_mtiles = (int)((nq + TM - 1) / TM);
     const int n_mpairs = (n_mtiles + QT - 1) / QT;
     const int64_t n_ntiles = (n + TN - 1) / TN;
@@ -712,6 +832,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     TuneCfg c{0, 0};
     if (cfg) c = *cfg;
     else tune_lookup(TUNE_TC, n, nq, k, &c);
+    const bool pre = want_prewiden(n, nq, c.b);
     const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_ntiles)
                                : pick_bf_splits(n_mpairs, n_ntiles, sms);
     const int64_t tiles_per_split = (n_ntiles + splits - 1) / splits;
@@ -725,9 +846,10 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     const size_t a_bytes = (size_t)n_mtiles * NCHUNK * A_STAGE;
     DT_CUDA_TRY(scratch.alloc(&a_exp, a_bytes));
     DT_CUDA_TRY(scratch.alloc(&qpop, (size_t)nq * 4));
-    DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_split * nq * k * 8));
+    const int n_lists = n_split * lists_per_unit(pre);
+    DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_lists * nq * k * 8));
     // lists start empty: a block that gives up on a wait leaves valid lists
-    DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_split * nq * k * 8, s));
+    DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_lists * nq * k * 8, s));
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
     const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
     widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, nq, n_mtiles, a_exp, qpop);
@@ -749,10 +871,19 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.n_units = nullptr;
     a.partial = partial;
     a.err = err;
-    bf_tc_kernel<MODE_PLAIN><<<grid, THREADS, smem_bytes(MODE_PLAIN), s>>>(a);
+    if (pre) {
+        unsigned char *b_exp = nullptr;
+        uint32_t *b_side = nullptr;
+        if (int r = prewiden_rows(db, n, scratch, s, &b_exp, &b_side)) return r;
+        a.b_exp = b_exp;
+        a.b_side = b_side;
+        bf_tc_kernel<MODE_PLAIN, true><<<grid, kernel_threads(true), smem_bytes(MODE_PLAIN), s>>>(a);
+    } else {
+        bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
+    }
     DT_CUDA_TRY(cudaGetLastError());
     *partial_out = partial;
-    *n_split_out = n_split;
+    *n_split_out = n_lists;
     return DT_OK;
 }
 
@@ -772,7 +903,7 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
                     const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
                     cudaStream_t s)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false>, (int)smem_bytes(MODE_PLAIN)));
     if (max_tiles <= 0) return DT_OK;
     unsigned char *a_exp = nullptr;
     uint32_t *qpop = nullptr, *err = nullptr;
@@ -797,7 +928,7 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.partial = partial;
     a.err = err;
     const int grid = (int)std::min<int64_t>(max_tiles, sm_count());   // units <= tiles
-    bf_tc_kernel<MODE_PLAIN><<<grid, THREADS, smem_bytes(MODE_PLAIN), s>>>(a);
+    bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
@@ -820,7 +951,7 @@ int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
                         const int64_t *n_units, int64_t max_units, int k, uint64_t *partial,
                         cudaStream_t s)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false>, (int)smem_bytes(MODE_PLAIN)));
     if (max_units <= 0) return DT_OK;
     uint32_t *err = nullptr;
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
@@ -837,7 +968,7 @@ int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
     a.partial = partial;
     a.err = err;
     const int grid = (int)std::min<int64_t>(max_units, sm_count());
-    bf_tc_kernel<MODE_PLAIN><<<grid, THREADS, smem_bytes(MODE_PLAIN), s>>>(a);
+    bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
@@ -848,8 +979,9 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
                    int64_t *need_words_out)
 {
     static_assert(TN == kScanTileRows, "scan tiles are tensor-core tiles");
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_BOUND>, (int)smem_bytes(MODE_BOUND)));
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_TREE>, (int)smem_bytes(MODE_TREE)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_BOUND, false>, (int)smem_bytes(MODE_BOUND)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_TREE, false>, (int)smem_bytes(MODE_TREE)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_TREE, true>, (int)smem_bytes(MODE_TREE)));
     const int64_t n = ix->n;
     const int64_t n_tt = (n + TN - 1) / TN;             // scan tiles
     const int64_t need_words = (n_tt + 31) / 32;
@@ -889,7 +1021,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     b.need_out = need;
     b.need_words = need_words;
     b.err = err;
-    bf_tc_kernel<MODE_BOUND><<<(int)std::min<int64_t>((int64_t)n_mpairs * b.n_split, sms), THREADS,
+    bf_tc_kernel<MODE_BOUND, false><<<(int)std::min<int64_t>((int64_t)n_mpairs * b.n_split, sms), kernel_threads(false),
                                smem_bytes(MODE_BOUND), s>>>(b);
     DT_CUDA_TRY(cudaGetLastError());
 
@@ -915,11 +1047,22 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     a.kmask = ix->tile_kmask;
     a.cap = cap_slot;
     a.err = err;
-    DT_CUDA_TRY(scratch.alloc(&partial, (size_t)a.n_split * nq * k * 8));
-    DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)a.n_split * nq * k * 8, s));
+    const bool pre = want_prewiden(n, nq, c.b);
+    const int n_lists = a.n_split * lists_per_unit(pre);
+    DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_lists * nq * k * 8));
+    DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_lists * nq * k * 8, s));
     a.partial = partial;
-    bf_tc_kernel<MODE_TREE><<<(int)std::min<int64_t>((int64_t)n_mpairs * a.n_split, sms), THREADS,
-                              smem_bytes(MODE_TREE), s>>>(a);
+    const int grid = (int)std::min<int64_t>((int64_t)n_mpairs * a.n_split, sms);
+    if (pre) {
+        unsigned char *b_exp = nullptr;
+        uint32_t *b_side = nullptr;
+        if (int r = prewiden_rows(ix->db_tree, n, scratch, s, &b_exp, &b_side)) return r;
+        a.b_exp = b_exp;
+        a.b_side = b_side;
+        bf_tc_kernel<MODE_TREE, true><<<grid, kernel_threads(true), smem_bytes(MODE_TREE), s>>>(a);
+    } else {
+        bf_tc_kernel<MODE_TREE, false><<<grid, kernel_threads(false), smem_bytes(MODE_TREE), s>>>(a);
+    }
     DT_CUDA_TRY(cudaGetLastError());
     if (need_host) {
         need_host->resize((size_t)n_mpairs * need_words);
@@ -927,7 +1070,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
                                     cudaMemcpyDeviceToHost, s));
     }
     *partial_out = partial;
-    *n_split_out = a.n_split;
+    *n_split_out = n_lists;
     *need_words_out = need_words;
     return DT_OK;
 }

@@ -236,7 +236,8 @@ namespace dtk {
 enum TuneKind { TUNE_TREE = 0, TUNE_POPC = 1, TUNE_TC = 2, TUNE_TREE_TC = 3 };
 struct TuneCfg {
     int a;   // TREE: threads per block; POPC / TC / TREE_TC: database splits
-    int b;   // TREE: resident blocks per SM
+    int b;   // TREE: resident blocks per SM; TC / TREE_TC: database rows widened
+             // in the kernel (1) or beforehand into scratch (2), 0 = automatic
 };
 bool tune_lookup(TuneKind kind, int64_t n, int64_t nq, int k, TuneCfg *cfg);
 void tune_store(TuneKind kind, int64_t n, int64_t nq, int k, const TuneCfg &cfg);
