@@ -361,11 +361,13 @@ int bf_search_noalloc(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int6
  * d_consumed: [nq] int64 descriptors drawn, or NULL.
  * engine selects how the nearest neighbours are found; every engine is
  *   exact, so the outputs do not depend on it: 1 = Dissimilarity Tree
- *   traversal (§4.2) of every descriptor in one persistent launch;
- *   2 = tensor-core scan of the index's database; 0 = automatic (2 when
- *   n_qdesc >= 256).  With T > 0, engine 2 searches the draws in rounds of
- *   32, 64, ... per undecided query, so mostly only the draws the loop
- *   consumes are searched.
+ *   traversal (§4.2), one warp per descriptor, all in one persistent
+ *   launch; 2 = tensor-core scan of the index's whole database; 3 = the
+ *   batched tree search of dt_search (descriptors of one partial query
+ *   share leaves, so their groups skip most of the database); 0 =
+ *   automatic (3 when n_qdesc >= 256, else 1).  With T > 0, engines 2 and
+ *   3 search the draws in rounds of T, 2T, ... per undecided query, so
+ *   mostly only the draws the loop consumes are searched.
  * With T = 0 the call does not synchronise the stream; with T > 0 and
  * engine 2 it reads each round's batch size back (synchronises).
  * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA, DT_ETIMEOUT.
@@ -407,22 +409,47 @@ int object_scores(const uint64_t *d_db, int64_t n, const uint32_t *d_object_of, 
 /*
  * dt_autotune — pick launch shapes by timing them on the caller's data.
  * The paper has no counterpart; results never depend on the shapes, only
- * speed.  With `index`, the tree traversal's threads per block and resident
- * blocks per SM are tuned for (index->n, nq, k); with `d_db`, the database
- * split counts of both brute-force paths are tuned for (n, nq, k).  The
- * winners go into a process-wide table keyed by (kind, log2 n, log2 nq, k,
- * SM count) that later calls of the same shape use.  Runs each candidate
- * twice (synchronises the stream).  `report` (nullable, host) receives the
- * chosen shapes and their times.  Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA.
+ * speed.  With `index`, the per-query traversal's threads per block and
+ * resident blocks per SM, and the batched traversal's database splits and
+ * database widening (inside the scan kernel, or once beforehand into
+ * scratch) are tuned for (index->n, nq, k); with `d_db`, the database
+ * split counts of both brute-force paths and the tensor path's widening
+ * are tuned for (n, nq, k).  The winners go into a process-wide table keyed
+ * by (kind, log2 n, log2 nq, k, SM count) that later calls of the same
+ * shape use.  Runs each candidate twice (synchronises the stream).
+ * `report` (nullable, host) receives the chosen shapes and their times.
+ * Errors: DT_EINVAL, DT_ENOMEM, DT_ECUDA.
  */
 typedef struct {
     int32_t tree_threads, tree_blocks_per_sm;
     int32_t popc_splits, tc_splits;
     float tree_ms, popc_ms, tc_ms;
     int32_t candidates_timed;
+    int32_t tc_prewiden;              /* 1: widened in the kernel, 2: beforehand */
+    int32_t tree_tc_splits, tree_tc_prewiden;
+    float tree_tc_ms;
+    int32_t retrieve_engine, retrieve_blocks_per_sm;
+    float retrieve_ms;
 } dt_tune_report;
 int dt_autotune(const dt_index *index, const uint64_t *d_db, int64_t n, const uint64_t *d_q,
                 int64_t nq, int32_t k, void *stream, dt_tune_report *report);
+
+/*
+ * dt_autotune_retrieve — pick how retrieve_objects finds the nearest
+ * neighbours by timing, on the caller's partial queries (the arguments as
+ * in retrieve_objects; a sample of the real workload is enough), every
+ * engine — for engine 1 also its resident blocks per SM, for engines 2 and
+ * 3 the launch of their batched search at this batch size (as dt_autotune)
+ * — and keeping the fastest for (index->n, threshold > 0).  Later calls of
+ * retrieve_objects with engine 0 use it.  The paper has no counterpart;
+ * the votes never depend on the choice.  Synchronises the stream.
+ * `report` (nullable) receives retrieve_engine, retrieve_blocks_per_sm and
+ * retrieve_ms (and candidates_timed).  Errors: as retrieve_objects.
+ */
+int dt_autotune_retrieve(const dt_index *index, const uint32_t *d_object_of_desc, int32_t n_objects,
+                         const uint64_t *d_qdesc, const int64_t *d_qoffsets, int32_t nq,
+                         int64_t n_qdesc, int32_t vote_threshold, void *stream,
+                         dt_tune_report *report);
 
 /* Save the tuning table to a text file / load one (returns the number of
  * entries loaded, or a negative status) / forget all entries. */
@@ -497,6 +524,26 @@ int ivf_search(const dt_ivf *ivf, const dt_encoder *enc, const uint64_t *d_q, in
  */
 void dt_debug_fail_allocation(int32_t nth);
 void dt_debug_inject_missing_copy(int32_t on);
+
+/*
+ * Kernel timing (the paper has no counterpart; for measurement).  While
+ * switched on, the library records a CUDA event pair around each launch of
+ * its main kernels, on the stream of the call (none during stream capture),
+ * and totals their durations per kernel name:
+ *   "tree_scan"   the batched tree search's scan (tensor cores)
+ *   "tree_bound"  its bound pass
+ *   "tc_scan"     bf_search's tensor-core scan
+ *   "popc_scan"   bf_search's popcount scan
+ *   "tree_warp"   the per-query tree traversal
+ *   "prewiden"    widening a database into FP8 stage images
+ * dt_kernel_timing(on) clears the totals and switches timing on (1) or off
+ * (0).  dt_kernel_time(name, &ms, &launches) waits for the recorded events
+ * of that kernel and returns their total time in milliseconds and the
+ * number of launches (0 and 0 for a name never recorded).
+ * Errors: DT_EINVAL (null arguments), DT_ECUDA.
+ */
+int dt_kernel_timing(int32_t on);
+int dt_kernel_time(const char *name, double *ms, int64_t *launches);
 
 /* Release an index (NULL is allowed).  Synchronises the device it lives on. */
 void dt_free(dt_index *index);

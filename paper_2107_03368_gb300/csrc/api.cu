@@ -80,6 +80,30 @@ cudaError_t allow_smem(const void *func, int bytes)
     return e;
 }
 
+// Kernel timing: event pairs per kernel name, read and released by
+// dt_kernel_time / dt_kernel_timing.
+static std::mutex g_timing_mu;
+static std::atomic<bool> g_timing_on{false};
+static std::vector<std::pair<std::string, std::pair<cudaEvent_t, cudaEvent_t>>> g_timing;
+
+bool kernel_timing_on() { return g_timing_on.load(); }
+
+void kernel_timing_add(const char *name, cudaEvent_t start, cudaEvent_t stop)
+{
+    std::lock_guard<std::mutex> lock(g_timing_mu);
+    g_timing.push_back({std::string(name), {start, stop}});
+}
+
+static void kernel_timing_clear()
+{
+    std::lock_guard<std::mutex> lock(g_timing_mu);
+    for (auto &e : g_timing) {
+        cudaEventDestroy(e.second.first);
+        cudaEventDestroy(e.second.second);
+    }
+    g_timing.clear();
+}
+
 // Test hook: when positive, the n-th scratch allocation from now fails.
 static std::atomic<int> g_fail_alloc{0};
 
@@ -363,7 +387,7 @@ int retrieve_objects(const dt_index *ix, const uint32_t *d_object_of_desc, int32
     DT_CHECK_ARG(nq >= 0, "nq must be >= 0");
     DT_CHECK_ARG(n_qdesc >= 0 && n_qdesc < (1LL << 31), "n_qdesc out of range");
     DT_CHECK_ARG(vote_threshold >= 0, "vote_threshold must be >= 0");
-    DT_CHECK_ARG(engine >= 0 && engine <= 2, "engine must be 0, 1 or 2");
+    DT_CHECK_ARG(engine >= 0 && engine <= 3, "engine must be 0, 1, 2 or 3");
     if (nq == 0) return DT_OK;
     REQUIRE_DEV(d_object_of_desc, "d_object_of_desc");
     REQUIRE_DEV(d_qdesc, "d_qdesc");
@@ -374,6 +398,35 @@ int retrieve_objects(const dt_index *ix, const uint32_t *d_object_of_desc, int32
     return launch_retrieve(ix, d_object_of_desc, n_objects, d_qdesc, d_qoffsets, nq, n_qdesc,
                            vote_threshold, seed, d_votes, d_winner, d_consumed, engine,
                            (cudaStream_t)stream);
+}
+
+int dt_kernel_timing(int32_t on)
+{
+    g_last_error.clear();
+    kernel_timing_clear();
+    g_timing_on.store(on != 0);
+    return DT_OK;
+}
+
+int dt_kernel_time(const char *name, double *ms, int64_t *launches)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(name != nullptr && ms != nullptr && launches != nullptr,
+                 "name, ms and launches must not be NULL");
+    std::lock_guard<std::mutex> lock(g_timing_mu);
+    double total = 0.0;
+    int64_t count = 0;
+    for (auto &e : g_timing) {
+        if (e.first != name) continue;
+        DT_CUDA_TRY(cudaEventSynchronize(e.second.second));
+        float t = 0.f;
+        DT_CUDA_TRY(cudaEventElapsedTime(&t, e.second.first, e.second.second));
+        total += t;
+        ++count;
+    }
+    *ms = total;
+    *launches = count;
+    return DT_OK;
 }
 
 void dt_debug_fail_allocation(int32_t nth) { g_fail_alloc.store(nth > 0 ? nth : 0); }

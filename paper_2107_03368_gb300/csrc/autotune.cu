@@ -8,7 +8,10 @@
 //   TC     tensor-core brute force: number of database splits (work units
 //          per persistent CTA), and whether the database is widened inside
 //          the kernel or once beforehand (b = 1 / 2);
-//   TREE_TC  the batched tree search's scan: the same two knobs.
+//   TREE_TC  the batched tree search's scan: the same two knobs;
+//   RETRIEVE the engine retrieve_objects uses when asked for engine 0, and
+//          engine 1's resident blocks per SM (keyed by the database size
+//          and whether the threshold is 0).
 // dt_autotune times each candidate on the caller's data with CUDA events
 // and keeps the fastest per key (kind, log2 n, log2 nq, k, SM count) in a
 // process-wide table; launchers look the key up and fall back to their
@@ -91,6 +94,38 @@ float time_call(F fn, cudaStream_t s)
     return ms;
 }
 
+// The batched traversal's scan: database splits x widening; each candidate
+// is put in the table for the call that times it, the fastest stays.
+int tune_tree_tc(const dt_index *ix, const uint64_t *d_q, int64_t nq, int k, uint32_t *idx,
+                 float *score, cudaStream_t s, dt_tune_report *report, int *tried)
+{
+    TuneCfg best{0, 0}, saved{0, 0};
+    const bool had = tune_lookup(TUNE_TREE_TC, ix->n, nq, k, &saved);
+    float best_ms = 1e30f;
+    for (int pre : {1, 2})
+        for (int splits : {4, 8, 16, 19, 32, 64}) {
+            const TuneCfg c{splits, pre};
+            tune_store(TUNE_TREE_TC, ix->n, nq, k, c);
+            float ms = time_call([&] {
+                return launch_dt_search_batched(ix, d_q, nq, k, nullptr, 0, idx, score, nullptr,
+                                                nullptr, s);
+            }, s);
+            ++*tried;
+            if (ms > 0.f && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    if (best.a) tune_store(TUNE_TREE_TC, ix->n, nq, k, best);
+    else if (had) tune_store(TUNE_TREE_TC, ix->n, nq, k, saved);
+    if (report && best.a) {
+        report->tree_tc_splits = best.a;
+        report->tree_tc_prewiden = best.b;
+        report->tree_tc_ms = best_ms;
+    }
+    return DT_OK;
+}
+
 }  // namespace
 }  // namespace dtk
 
@@ -137,21 +172,27 @@ int dt_autotune(const dt_index *ix, const uint64_t *d_db, int64_t n, const uint6
             }
         }
     }
+    if (ix) {
+        if (int r = tune_tree_tc(ix, d_q, nq, k, idx, score, s, report, &tried)) return r;
+    }
     if (d_db) {
         for (int kind = TUNE_POPC; kind <= TUNE_TC; ++kind) {
             TuneCfg best{0, 0};
             float best_ms = 1e30f;
-            for (int splits : {1, 2, 4, 8, 16, 32, 64, 128}) {
-                TuneCfg c{splits, 0};
-                float ms = time_call([&] {
-                    return kind == TUNE_POPC
-                               ? launch_bf_popc_cfg(d_db, n, d_q, nq, k, idx, score, nullptr, s, &c)
-                               : launch_bf_tc_cfg(d_db, n, d_q, nq, k, idx, score, nullptr, s, &c);
-                }, s);
-                ++tried;
-                if (ms > 0.f && ms < best_ms) {
-                    best_ms = ms;
-                    best = c;
+            for (int pre : {0, 1, 2}) {
+                if ((kind == TUNE_POPC) != (pre == 0)) continue;   // widening: tensor path only
+                for (int splits : {1, 2, 4, 8, 16, 32, 64, 128}) {
+                    TuneCfg c{splits, pre};
+                    float ms = time_call([&] {
+                        return kind == TUNE_POPC
+                                   ? launch_bf_popc_cfg(d_db, n, d_q, nq, k, idx, score, nullptr, s, &c)
+                                   : launch_bf_tc_cfg(d_db, n, d_q, nq, k, idx, score, nullptr, s, &c);
+                    }, s);
+                    ++tried;
+                    if (ms > 0.f && ms < best_ms) {
+                        best_ms = ms;
+                        best = c;
+                    }
                 }
             }
             if (best.a) {
@@ -162,6 +203,7 @@ int dt_autotune(const dt_index *ix, const uint64_t *d_db, int64_t n, const uint6
                         report->popc_ms = best_ms;
                     } else {
                         report->tc_splits = best.a;
+                        report->tc_prewiden = best.b;
                         report->tc_ms = best_ms;
                     }
                 }
@@ -171,6 +213,62 @@ int dt_autotune(const dt_index *ix, const uint64_t *d_db, int64_t n, const uint6
     DT_CUDA_TRY(cudaStreamSynchronize(s));
     if (report) report->candidates_timed = tried;
     return DT_OK;
+}
+
+int dt_autotune_retrieve(const dt_index *ix, const uint32_t *d_object_of_desc, int32_t n_objects,
+                         const uint64_t *d_qdesc, const int64_t *d_qoffsets, int32_t nq,
+                         int64_t n_qdesc, int32_t vote_threshold, void *stream,
+                         dt_tune_report *report)
+{
+    if (report) *report = dt_tune_report{};
+    DT_CHECK_ARG(ix != nullptr && d_object_of_desc != nullptr && d_qdesc != nullptr &&
+                 d_qoffsets != nullptr, "index, object ids, query descriptors and offsets required");
+    DT_CHECK_ARG(n_objects >= 1 && nq >= 1 && n_qdesc >= 1 && n_qdesc < (1LL << 31) &&
+                 vote_threshold >= 0, "sizes out of range");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch scratch(s);
+    uint32_t *votes = nullptr;
+    int32_t *winner = nullptr;
+    int64_t *consumed = nullptr;
+    DT_CUDA_TRY(scratch.alloc(&votes, (size_t)nq * n_objects * 4));
+    DT_CUDA_TRY(scratch.alloc(&winner, (size_t)nq * 4));
+    DT_CUDA_TRY(scratch.alloc(&consumed, (size_t)nq * 8));
+    // the batched search behind engine 3 at this batch size first
+    dt_tune_report sub{};
+    int tried = 0;
+    if (vote_threshold == 0) {
+        uint32_t *nn = nullptr;
+        float *sc = nullptr;
+        DT_CUDA_TRY(scratch.alloc(&nn, (size_t)n_qdesc * 4));
+        DT_CUDA_TRY(scratch.alloc(&sc, (size_t)n_qdesc * 4));
+        if (int r = tune_tree_tc(ix, d_qdesc, n_qdesc, 1, nn, sc, s, &sub, &tried)) return r;
+    }
+    const int key_nq = vote_threshold > 0 ? 2 : 1;
+    TuneCfg best{0, 0};
+    float best_ms = 1e30f;
+    const TuneCfg cands[] = {{1, 0}, {1, 2}, {1, 4}, {2, 0}, {3, 0}};
+    for (const TuneCfg &c : cands) {
+        float ms = time_call([&] {
+            return launch_retrieve(ix, d_object_of_desc, n_objects, d_qdesc, d_qoffsets, nq, n_qdesc,
+                                   vote_threshold, 0x9e3779b97f4a7c15ull, votes, winner, consumed, 0,
+                                   s, &c);
+        }, s);
+        ++tried;
+        if (ms > 0.f && ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    DT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (best.a) tune_store(TUNE_RETRIEVE, ix->n, key_nq, 1, best);
+    if (report) {
+        *report = sub;
+        report->retrieve_engine = best.a;
+        report->retrieve_blocks_per_sm = best.b;
+        report->retrieve_ms = best.a ? best_ms : 0.f;
+        report->candidates_timed = tried;
+    }
+    return best.a ? DT_OK : DT_ECUDA;
 }
 
 int dt_tune_save(const char *path)
@@ -195,7 +293,7 @@ int dt_tune_load(const char *path)
     std::lock_guard<std::mutex> lock(g_tune_mu);
     int kind, nl, ql, k, sms, a, b, loaded = 0;
     while (std::fscanf(f, "%d %d %d %d %d %d %d", &kind, &nl, &ql, &k, &sms, &a, &b) == 7) {
-        if (kind < TUNE_TREE || kind > TUNE_TREE_TC || a <= 0 || b < 0) continue;
+        if (kind < TUNE_TREE || kind > TUNE_RETRIEVE || a <= 0 || b < 0) continue;
         g_tune[Key(kind, nl, ql, k, sms)] = TuneCfg{a, b};
         ++loaded;
     }

@@ -331,8 +331,11 @@ int launch_bf_popc_cfg(const uint64_t *db, int64_t n, const uint64_t *q, int64_t
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_bf_error));
     dim3 grid((unsigned)qblocks, (unsigned)n_split);
     const bool drop = g_drop_copy.load() != 0;
-    bf_popc_kernel<<<grid, THREADS, smem, s>>>(db, n, q, nq, k, tiles_per_split, partial, err,
-                                               drop ? 4096u : kSpinLimit, drop ? 0 : -1);
+    {
+        KernelTimer timer("popc_scan", s);
+        bf_popc_kernel<<<grid, THREADS, smem, s>>>(db, n, q, nq, k, tiles_per_split, partial, err,
+                                                   drop ? 4096u : kSpinLimit, drop ? 0 : -1);
+    }
     DT_CUDA_TRY(cudaGetLastError());
     const int wpb = 8;
     bf_merge_kernel<<<(unsigned)((nq + wpb - 1) / wpb), wpb * 32, 0, s>>>(partial, n_split, db, n,

@@ -267,8 +267,9 @@ struct TcArgs {
     const uint32_t *idx_map;         // row -> reported index (nullable: identity)
     int64_t nq;
     int k;
-    int n_mtiles;
-    int n_mpairs;                    // units per split: ceil(n_mtiles / 2)
+    int n_mtiles;                    // query tiles of the whole call
+    int n_mpairs;                    // split mode: pairs of query tiles in this launch
+    int64_t mp_base;                 // split mode: first pair of this launch
     int64_t n_ntiles;
     int64_t tiles_per_split;
     int n_split;
@@ -328,7 +329,7 @@ __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
         v.nvalid[0] = t.nvalid0;
         v.nvalid[1] = t.a_tile1 >= 0 ? t.nvalid1 : 0;
     } else {
-        const int64_t mp = u % a.n_mpairs;
+        const int64_t mp = a.mp_base + u % a.n_mpairs;
         v.sp = u / a.n_mpairs;
         v.mp = mp;
         v.out_base = 0;
@@ -779,6 +780,12 @@ __global__ void merge_top1_kernel(const uint64_t *__restrict__ partial, int n_sp
     if (lane == 0) nn[q] = best == kEmpty ? 0xFFFFFFFFu : (uint32_t)best;
 }
 
+// Split-mode scans run over at most this many pairs of query tiles per
+// launch: 96 pre-widened query tiles (48 MB) stay resident in L2 while the
+// database streams past, instead of being fetched from HBM again for every
+// database tile when a call has more queries than L2 holds.
+constexpr int kBatchPairs = 48;
+
 // Should a split-mode scan of n rows by nq queries read a pre-widened copy
 // of the rows (kernel variant PRE)?  The copy costs one pass writing
 // n * 4 KB (8x the rows) and that much scratch; it spares every unit the
@@ -810,9 +817,12 @@ int prewiden_rows(const uint64_t *db, int64_t n, Scratch &scratch, cudaStream_t 
     DT_CUDA_TRY(scratch.alloc(&rowpop, (size_t)n_tiles * TN * 4));
     static_assert(TN == TM && B_STAGE == A_STAGE, "database tiles widen like query tiles");
     const int64_t items = n_tiles * TN * NCHUNK;
-    widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(db, n, (int)n_tiles, *b_exp,
-                                                                         rowpop);
-    side_kernel<<<(unsigned)n_tiles, TN, 0, s>>>(rowpop, n, *b_side);
+    {
+        KernelTimer timer("prewiden", s);
+        widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(db, n, (int)n_tiles, *b_exp,
+                                                                             rowpop);
+        side_kernel<<<(unsigned)n_tiles, TN, 0, s>>>(rowpop, n, *b_side);
+    }
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
@@ -833,12 +843,11 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     if (cfg) c = *cfg;
     else tune_lookup(TUNE_TC, n, nq, k, &c);
     const bool pre = want_prewiden(n, nq, c.b);
+    const int batch_pairs = std::min(n_mpairs, kBatchPairs);
     const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_ntiles)
-                               : pick_bf_splits(n_mpairs, n_ntiles, sms);
+                               : pick_bf_splits(batch_pairs, n_ntiles, sms);
     const int64_t tiles_per_split = (n_ntiles + splits - 1) / splits;
     const int n_split = (int)((n_ntiles + tiles_per_split - 1) / tiles_per_split);
-    const int64_t units = (int64_t)n_mpairs * n_split;
-    const int grid = (int)std::min<int64_t>(units, sms);
 
     unsigned char *a_exp = nullptr;
     uint32_t *qpop = nullptr, *err = nullptr;
@@ -877,11 +886,18 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
         if (int r = prewiden_rows(db, n, scratch, s, &b_exp, &b_side)) return r;
         a.b_exp = b_exp;
         a.b_side = b_side;
-        bf_tc_kernel<MODE_PLAIN, true><<<grid, kernel_threads(true), smem_bytes(MODE_PLAIN), s>>>(a);
-    } else {
-        bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
     }
-    DT_CUDA_TRY(cudaGetLastError());
+    for (int p0 = 0; p0 < n_mpairs; p0 += kBatchPairs) {     // L2-sized batches of queries
+        a.mp_base = p0;
+        a.n_mpairs = std::min(kBatchPairs, n_mpairs - p0);
+        const int grid = (int)std::min<int64_t>((int64_t)a.n_mpairs * n_split, sms);
+        KernelTimer timer("tc_scan", s);
+        if (pre)
+            bf_tc_kernel<MODE_PLAIN, true><<<grid, kernel_threads(true), smem_bytes(MODE_PLAIN), s>>>(a);
+        else
+            bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
+        DT_CUDA_TRY(cudaGetLastError());
+    }
     *partial_out = partial;
     *n_split_out = n_lists;
     return DT_OK;
@@ -1012,8 +1028,9 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     b.n_mtiles = n_mtiles;
     b.n_mpairs = n_mpairs;
     b.n_ntiles = (n_tt + TN - 1) / TN;
+    const int batch_pairs = std::min(n_mpairs, kBatchPairs);
     {
-        const int splits = pick_bf_splits(n_mpairs, b.n_ntiles, sms);
+        const int splits = pick_bf_splits(batch_pairs, b.n_ntiles, sms);
         b.tiles_per_split = (b.n_ntiles + splits - 1) / splits;
         b.n_split = (int)((b.n_ntiles + b.tiles_per_split - 1) / b.tiles_per_split);
     }
@@ -1021,8 +1038,13 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     b.need_out = need;
     b.need_words = need_words;
     b.err = err;
-    bf_tc_kernel<MODE_BOUND, false><<<(int)std::min<int64_t>((int64_t)n_mpairs * b.n_split, sms), kernel_threads(false),
-                               smem_bytes(MODE_BOUND), s>>>(b);
+    for (int p0 = 0; p0 < n_mpairs; p0 += kBatchPairs) {     // L2-sized batches of queries
+        b.mp_base = p0;
+        b.n_mpairs = std::min(kBatchPairs, n_mpairs - p0);
+        KernelTimer timer("tree_bound", s);
+        bf_tc_kernel<MODE_BOUND, false><<<(int)std::min<int64_t>((int64_t)b.n_mpairs * b.n_split, sms),
+                                           kernel_threads(false), smem_bytes(MODE_BOUND), s>>>(b);
+    }
     DT_CUDA_TRY(cudaGetLastError());
 
     // pass 2: the needed scan tiles of each pair, zero K chunks skipped
@@ -1039,7 +1061,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     a.n_ntiles = n_tt;
     TuneCfg c{0, 0};
     tune_lookup(TUNE_TREE_TC, n, nq, k, &c);
-    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_tt) : pick_bf_splits(n_mpairs, n_tt, sms);
+    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_tt) : pick_bf_splits(batch_pairs, n_tt, sms);
     a.tiles_per_split = (n_tt + splits - 1) / splits;
     a.n_split = (int)((n_tt + a.tiles_per_split - 1) / a.tiles_per_split);
     a.need = need;
@@ -1052,16 +1074,23 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_lists * nq * k * 8));
     DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_lists * nq * k * 8, s));
     a.partial = partial;
-    const int grid = (int)std::min<int64_t>((int64_t)n_mpairs * a.n_split, sms);
     if (pre) {
         unsigned char *b_exp = nullptr;
         uint32_t *b_side = nullptr;
         if (int r = prewiden_rows(ix->db_tree, n, scratch, s, &b_exp, &b_side)) return r;
         a.b_exp = b_exp;
         a.b_side = b_side;
-        bf_tc_kernel<MODE_TREE, true><<<grid, kernel_threads(true), smem_bytes(MODE_TREE), s>>>(a);
-    } else {
-        bf_tc_kernel<MODE_TREE, false><<<grid, kernel_threads(false), smem_bytes(MODE_TREE), s>>>(a);
+    }
+    for (int p0 = 0; p0 < n_mpairs; p0 += kBatchPairs) {     // L2-sized batches of queries
+        a.mp_base = p0;
+        a.n_mpairs = std::min(kBatchPairs, n_mpairs - p0);
+        const int grid = (int)std::min<int64_t>((int64_t)a.n_mpairs * a.n_split, sms);
+        KernelTimer timer("tree_scan", s);
+        if (pre)
+            bf_tc_kernel<MODE_TREE, true><<<grid, kernel_threads(true), smem_bytes(MODE_TREE), s>>>(a);
+        else
+            bf_tc_kernel<MODE_TREE, false><<<grid, kernel_threads(false), smem_bytes(MODE_TREE), s>>>(a);
+        DT_CUDA_TRY(cudaGetLastError());
     }
     DT_CUDA_TRY(cudaGetLastError());
     if (need_host) {

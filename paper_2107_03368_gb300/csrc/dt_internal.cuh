@@ -193,6 +193,46 @@ struct Grow {
 
 int sm_count();
 
+// Kernel timing (dt_kernel_timing / dt_kernel_time): while switched on, a
+// KernelTimer around a launch records a CUDA event pair on its stream
+// (nothing under stream capture, nothing while off), totalled per name.
+bool kernel_timing_on();
+void kernel_timing_add(const char *name, cudaEvent_t start, cudaEvent_t stop);
+class KernelTimer {
+  public:
+    KernelTimer(const char *name, cudaStream_t s) : name_(name), s_(s)
+    {
+        if (!kernel_timing_on()) return;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return;
+        }
+        if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        on_ = cudaEventRecord(a_, s) == cudaSuccess;
+    }
+    ~KernelTimer()
+    {
+        if (on_ && cudaEventRecord(b_, s_) == cudaSuccess) {
+            kernel_timing_add(name_, a_, b_);
+            return;
+        }
+        if (a_) cudaEventDestroy(a_);
+        if (b_) cudaEventDestroy(b_);
+    }
+    KernelTimer(const KernelTimer &) = delete;
+    KernelTimer &operator=(const KernelTimer &) = delete;
+
+  private:
+    const char *name_;
+    cudaStream_t s_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+    bool on_ = false;
+};
+
 // Let `func` use `bytes` of dynamic shared memory on the current device (a
 // per-device setting, applied once per kernel and device).
 cudaError_t allow_smem(const void *func, int bytes);
@@ -233,11 +273,12 @@ struct dt_index {
 
 namespace dtk {
 // Autotuner table (autotune.cu): a launch shape per kernel kind and problem size.
-enum TuneKind { TUNE_TREE = 0, TUNE_POPC = 1, TUNE_TC = 2, TUNE_TREE_TC = 3 };
+enum TuneKind { TUNE_TREE = 0, TUNE_POPC = 1, TUNE_TC = 2, TUNE_TREE_TC = 3, TUNE_RETRIEVE = 4 };
 struct TuneCfg {
     int a;   // TREE: threads per block; POPC / TC / TREE_TC: database splits
     int b;   // TREE: resident blocks per SM; TC / TREE_TC: database rows widened
-             // in the kernel (1) or beforehand into scratch (2), 0 = automatic
+             // in the kernel (1) or beforehand into scratch (2), 0 = automatic;
+             // RETRIEVE: a = engine (1-3), b = engine 1's resident blocks per SM
 };
 bool tune_lookup(TuneKind kind, int64_t n, int64_t nq, int k, TuneCfg *cfg);
 void tune_store(TuneKind kind, int64_t n, int64_t nq, int k, const TuneCfg &cfg);
@@ -311,10 +352,12 @@ int launch_quicci(const float *d_vertices, int64_t n_vertices, const int32_t *d_
                   cudaStream_t s);
 int launch_dt_search(const dt_index *ix, const uint64_t *q, int64_t nq, int k, uint32_t *idx,
                      float *score, uint16_t *ab, dt_stats *stats, cudaStream_t s);
+// cfg (nullable): the engine (a, used when engine is 0) and engine 1's
+// resident blocks per SM (b); NULL: the tuning table, else defaults.
 int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects,
                     const uint64_t *qdesc, const int64_t *qoffsets, int nq, int64_t total,
                     int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
-                    int64_t *consumed, int engine, cudaStream_t s);
+                    int64_t *consumed, int engine, cudaStream_t s, const TuneCfg *cfg = nullptr);
 // Work unit of the tensor-core scan in list mode: the query tiles a_tile0
 // and a_tile1 (TM rows each, the first nvalid0 / nvalid1 of them real;
 // a_tile1 < 0: none) against database rows [row0, row1).  Results go to

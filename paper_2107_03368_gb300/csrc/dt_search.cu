@@ -375,8 +375,11 @@ int launch_dt_search_cfg(const dt_index *ix, const uint64_t *q, int64_t nq, int 
     DT_CUDA_TRY(scratch.alloc(&ctl, sizeof(SearchCtl)));
     DT_CUDA_TRY(scratch.alloc(&stacks, (size_t)nwarps * stack_cap * 8));
     DT_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(SearchCtl), s));
-    kern<<<(unsigned)blocks, nt, 0, s>>>(tv, ix->iperm, q, nq, k, seeds, n_seed, ix->n, stacks,
-                                         stack_cap, ctl, idx, score, ab);
+    {
+        KernelTimer timer("tree_warp", s);
+        kern<<<(unsigned)blocks, nt, 0, s>>>(tv, ix->iperm, q, nq, k, seeds, n_seed, ix->n, stacks,
+                                             stack_cap, ctl, idx, score, ab);
+    }
     DT_CUDA_TRY(cudaGetLastError());
     int rc = DT_OK;
     if (stats) {

@@ -283,7 +283,8 @@ __global__ void round_finish_kernel(const uint32_t *__restrict__ votes, int n_ob
 
 int retrieve_tree(const dt_index *ix, const uint32_t *object_of, int n_objects, const uint64_t *qdesc,
                   const int64_t *qoffsets, int nq, int64_t total, int threshold, uint64_t seed,
-                  uint32_t *votes, int32_t *winner, int64_t *consumed, cudaStream_t s)
+                  uint32_t *votes, int32_t *winner, int64_t *consumed, int blocks_per_sm,
+                  cudaStream_t s)
 {
     TreeView tv{ix->node, ix->or_img, ix->and_img, ix->db_tree, ix->perm};
     const bool use_and = ix->use_and != 0;
@@ -299,6 +300,7 @@ int retrieve_tree(const dt_index *ix, const uint32_t *object_of, int n_objects, 
     auto kern = threshold > 0 ? k1 : k0;
     int per_sm = 0;
     DT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, VT, 0));
+    if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);   // fewer descriptors in flight
     int64_t blocks = std::max(1, per_sm) * (int64_t)sm_count();
     blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (total + 7) / 8));
     const int64_t nwarps = blocks * (VT / 32);
@@ -321,17 +323,32 @@ int retrieve_tree(const dt_index *ix, const uint32_t *object_of, int n_objects, 
     return DT_OK;
 }
 
-int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects,
-                    const uint64_t *qdesc, const int64_t *qoffsets, int nq, int64_t total,
-                    int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
-                    int64_t *consumed, cudaStream_t s)
+// Nearest database descriptor (original index) of each of m query
+// descriptors: the tensor-core brute force over the tree-ordered rows, or
+// the batched tree search (top-1).  Both break ties by lowest index.
+int nearest(const dt_index *ix, const uint64_t *q, int64_t m, uint32_t *nn, bool tree,
+            cudaStream_t s)
+{
+    if (!tree) return launch_tc_top1(ix->db_tree, ix->n, ix->perm, q, m, nn, s);
+    Scratch scratch(s);
+    float *score = nullptr;
+    DT_CUDA_TRY(scratch.alloc(&score, (size_t)m * 4));
+    return launch_dt_search_batched(ix, q, m, 1, nullptr, 0, nn, score, nullptr, nullptr, s);
+}
+
+// Engines 2 (tree = false) and 3 (tree = true): every query descriptor's
+// nearest neighbour in one batched search (T = 0), or in rounds of draws.
+int retrieve_batched(const dt_index *ix, const uint32_t *object_of, int n_objects,
+                     const uint64_t *qdesc, const int64_t *qoffsets, int nq, int64_t total,
+                     int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
+                     int64_t *consumed, bool tree, cudaStream_t s)
 {
     Scratch scratch(s);
     if (threshold == 0) {
         uint32_t *nn = nullptr;
         DT_CUDA_TRY(scratch.alloc(&nn, (size_t)std::max<int64_t>(total, 1) * 4));
         if (total > 0) {
-            if (int r = launch_tc_top1(ix->db_tree, ix->n, ix->perm, qdesc, total, nn, s)) return r;
+            if (int r = nearest(ix, qdesc, total, nn, tree, s)) return r;
             vote_all_kernel<<<(unsigned)std::min<int64_t>((total + 255) / 256, 4096), 256, 0, s>>>(
                 nn, total, object_of, n_objects, qoffsets, nq, votes);
         }
@@ -378,7 +395,7 @@ int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects
             break;
         }
         round_gather_kernel<<<(nq + 7) / 8, 256, 0, s>>>(qdesc, qoffsets, nq, order, st, batch);
-        rc = launch_tc_top1(ix->db_tree, ix->n, ix->perm, batch, batch_n, nn, s);
+        rc = nearest(ix, batch, batch_n, nn, tree, s);
         if (rc == DT_OK)
             round_replay_kernel<<<(nq + 127) / 128, 128, 0, s>>>(nn, object_of, n_objects, qoffsets,
                                                                 nq, threshold, st, votes, winner);
@@ -396,15 +413,19 @@ int retrieve_tensor(const dt_index *ix, const uint32_t *object_of, int n_objects
 int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects,
                     const uint64_t *qdesc, const int64_t *qoffsets, int nq, int64_t total,
                     int threshold, uint64_t seed, uint32_t *votes, int32_t *winner,
-                    int64_t *consumed, int engine, cudaStream_t s)
+                    int64_t *consumed, int engine, cudaStream_t s, const TuneCfg *cfg)
 {
     DT_CUDA_TRY(cudaMemsetAsync(votes, 0, (size_t)nq * n_objects * 4, s));
-    if (engine == 0) engine = total >= 256 ? 2 : 1;
-    if (engine == 2)
-        return retrieve_tensor(ix, object_of, n_objects, qdesc, qoffsets, nq, total, threshold, seed,
-                               votes, winner, consumed, s);
+    // the autotuner's choice for this database size and kind of threshold
+    TuneCfg c{0, 0};
+    if (cfg) c = *cfg;
+    else tune_lookup(TUNE_RETRIEVE, ix->n, threshold > 0 ? 2 : 1, 1, &c);
+    if (engine == 0) engine = c.a >= 1 && c.a <= 3 ? c.a : (total >= 256 ? 3 : 1);
+    if (engine >= 2)
+        return retrieve_batched(ix, object_of, n_objects, qdesc, qoffsets, nq, total, threshold,
+                                seed, votes, winner, consumed, engine == 3, s);
     return retrieve_tree(ix, object_of, n_objects, qdesc, qoffsets, nq, total, threshold, seed, votes,
-                         winner, consumed, s);
+                         winner, consumed, c.b, s);
 }
 
 }  // namespace dtk

@@ -53,7 +53,10 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("tree_threads", ctypes.c_int32), ("tree_blocks_per_sm", ctypes.c_int32),
                 ("popc_splits", ctypes.c_int32), ("tc_splits", ctypes.c_int32),
                 ("tree_ms", ctypes.c_float), ("popc_ms", ctypes.c_float), ("tc_ms", ctypes.c_float),
-                ("candidates_timed", ctypes.c_int32)]
+                ("candidates_timed", ctypes.c_int32), ("tc_prewiden", ctypes.c_int32),
+                ("tree_tc_splits", ctypes.c_int32), ("tree_tc_prewiden", ctypes.c_int32),
+                ("tree_tc_ms", ctypes.c_float), ("retrieve_engine", ctypes.c_int32),
+                ("retrieve_blocks_per_sm", ctypes.c_int32), ("retrieve_ms", ctypes.c_float)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -92,8 +95,11 @@ def load():
             "dt_sync_status": ([P], ctypes.c_int),
             "object_scores": ([P, i64, P, i32, P, P, i32, i64, P, P], ctypes.c_int),
             "dt_debug_fail_allocation": ([i32], None),
+            "dt_kernel_timing": ([i32], ctypes.c_int),
+            "dt_kernel_time": ([ctypes.c_char_p, P, P], ctypes.c_int),
             "dt_debug_inject_missing_copy": ([i32], None),
             "dt_autotune": ([P, P, i64, P, i64, i32, P, P], ctypes.c_int),
+            "dt_autotune_retrieve": ([P, P, i32, P, P, i32, i64, i32, P, P], ctypes.c_int),
             "dt_tune_save": ([ctypes.c_char_p], ctypes.c_int),
             "dt_tune_load": ([ctypes.c_char_p], ctypes.c_int),
             "dt_tune_clear": ([], None),
@@ -317,8 +323,8 @@ def bf_search_noalloc(db, q, k, out, stream=None):
 def retrieve_objects(index: Index, object_of, n_objects, qdesc, qoffsets, vote_threshold=0,
                      seed=0, with_consumed=True, engine=0, out=None, stream=None):
     """Returns (votes int32 [nq, n_objects] (uint32 counts), winner int32 [nq],
-    consumed int64 [nq] or None).  engine: 0 auto, 1 tree traversal,
-    2 tensor-core scan (identical results)."""
+    consumed int64 [nq] or None).  engine: 0 auto, 1 tree traversal per
+    descriptor, 2 tensor-core scan, 3 batched tree search (identical results)."""
     qdesc = _desc(qdesc, "qdesc")
     if not (object_of.is_cuda and object_of.dtype == torch.int32 and object_of.is_contiguous()):
         raise ValueError("object_of must be a contiguous CUDA int32 tensor")
@@ -349,6 +355,19 @@ def dt_autotune(index=None, db=None, q=None, k=10, stream=None):
     _check(load().dt_autotune(index.handle if index is not None else None, _ptr(db),
                               db.shape[0] if db is not None else 0, _ptr(q), q.shape[0], k,
                               _stream(stream), ctypes.byref(rep)), "dt_autotune")
+    return rep.as_dict()
+
+
+def dt_autotune_retrieve(index: Index, object_of, n_objects, qdesc, qoffsets, vote_threshold=0,
+                         stream=None):
+    """Time retrieve_objects' engines on these partial queries (a sample of
+    the workload) and remember the fastest for engine 0 (returns the report)."""
+    qdesc = _desc(qdesc, "qdesc")
+    rep = TuneReport()
+    _check(load().dt_autotune_retrieve(index.handle, _ptr(object_of), n_objects, _ptr(qdesc),
+                                       _ptr(qoffsets), qoffsets.shape[0] - 1, qdesc.shape[0],
+                                       vote_threshold, _stream(stream), ctypes.byref(rep)),
+           "dt_autotune_retrieve")
     return rep.as_dict()
 
 
@@ -385,6 +404,20 @@ def object_scores(db, object_of, n_objects, qdesc, qoffsets, stream=None):
                                 _ptr(qoffsets), nq, qdesc.shape[0], _ptr(out), _stream(stream)),
            "object_scores")
     return out
+
+
+def dt_kernel_timing(on):
+    """Clear the kernel timing totals and switch timing on or off."""
+    _check(load().dt_kernel_timing(1 if on else 0), "dt_kernel_timing")
+
+
+def dt_kernel_time(name):
+    """(total milliseconds, launches) of the named kernel since timing was
+    switched on (see include/dt.h for the names)."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(load().dt_kernel_time(name.encode(), ctypes.byref(ms), ctypes.byref(n)),
+           "dt_kernel_time")
+    return ms.value, n.value
 
 
 def dt_debug_fail_allocation(nth):

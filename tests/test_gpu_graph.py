@@ -56,7 +56,7 @@ def test_graph_replay_retrieve():
     ix = dt.dt_build(to_dev(db))
     d_obj = torch.from_numpy(obj.view(np.int32)).cuda()
     d_qd, d_off = to_dev(qd), torch.from_numpy(off).cuda()
-    for engine in (1, 2):
+    for engine in (1, 2, 3):
         fn = lambda: dt.retrieve_objects(ix, d_obj, n_obj, d_qd, d_off, 0, seed, engine=engine)
         g, out = _capture(fn)
         g.replay()

@@ -120,8 +120,10 @@ def test_insert_at_full_size(big):
 
 
 def test_partial_retrieval_on_full_database():
-    """Threshold 0 on a subset of uneven queries with both engines; threshold
-    10 on all 1,000 queries with the round-based tensor engine."""
+    """Threshold 0 on a subset of uneven queries with every engine; threshold
+    10 on all 1,000 queries with the round-based tensor engine; threshold 0
+    on 60 queries (about 340,000 query descriptors) with the batched tree
+    engine, sampled queries checked against their brute-force neighbours."""
     n_obj, per = 400, 25_000
     db, obj = synth.database(SEED + 2, n_obj * per, per_object=per)
     qd, off, qobj = synth.partial_queries(SEED + 2, db, n_obj, per, 1000)
@@ -141,6 +143,10 @@ def test_partial_retrieval_on_full_database():
                                                         engine=1)
     assert torch.equal(votes, votes_t) and torch.equal(winner, winner_t)
     assert torch.equal(consumed, consumed_t)
+    r3 = dt.retrieve_objects(ix, d_obj, n_obj, d_qd, torch.from_numpy(off_s).cuda(), 0, SEED,
+                             engine=3)
+    for x, y in zip(r3, (votes, winner, consumed)):
+        assert torch.equal(x, y)
     b_idx, _, _ = dt.bf_search(d_db, d_qd, 1)
     nn = idx_np(b_idx)[:, 0]
     v = votes.cpu().numpy().view(np.uint32)
@@ -158,8 +164,10 @@ def test_partial_retrieval_on_full_database():
                              engine=2)
     r1 = dt.retrieve_objects(ix, d_obj, n_obj, d_qd, torch.from_numpy(off_s).cuda(), 10, SEED,
                              engine=1)
-    for x, y in zip(r1, r2):
-        assert torch.equal(x, y)
+    r3 = dt.retrieve_objects(ix, d_obj, n_obj, d_qd, torch.from_numpy(off_s).cuda(), 10, SEED,
+                             engine=3)
+    for x, y, z in zip(r1, r2, r3):
+        assert torch.equal(x, y) and torch.equal(x, z)
     # threshold 10 on all 1,000 partial queries: the winner reaches exactly 10
     # votes, every vote is a draw, and the draws replay the oracle's order
     votes10, winner10, used10 = dt.retrieve_objects(ix, d_obj, n_obj, to_dev(qd),
@@ -175,6 +183,22 @@ def test_partial_retrieval_on_full_database():
     o_nn, _, _ = oracle.bf_topk(db, qd[off[j] + order], 1)
     expect = np.bincount(obj[o_nn[:, 0]], minlength=n_obj)
     assert np.array_equal(v10[j], expect)
+
+    # threshold 0 on 60 of the partial queries (about 340,000 descriptors)
+    # with the batched tree engine
+    m = 60
+    off, qobj = off[: m + 1].copy(), qobj[:m]
+    d_all, d_off = to_dev(qd[: off[-1]]), torch.from_numpy(off).cuda()
+    votes0, winner0, used0 = dt.retrieve_objects(ix, d_obj, n_obj, d_all, d_off, 0, SEED, engine=3)
+    v0 = votes0.cpu().numpy().view(np.uint32)
+    assert np.array_equal(v0.sum(1), np.diff(off))
+    assert np.array_equal(used0.cpu().numpy(), np.diff(off))
+    for j in (0, 31, m - 1):
+        q_j = to_dev(qd[off[j]:off[j + 1]])
+        nn_j = idx_np(dt.bf_search(d_db, q_j, 1, path=2)[0])[:, 0]
+        assert np.array_equal(v0[j], np.bincount(obj[nn_j], minlength=n_obj))
+        assert winner0[j].item() == int(np.argmax(v0[j]))
+    assert (winner0.cpu().numpy() == qobj).mean() > 0.95
     ix.free()
 
 

@@ -11,7 +11,7 @@ from paper_2107_03368_gb300 import dt, synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("engine", [1, 2])
+@pytest.mark.parametrize("engine", [1, 2, 3])
 @pytest.mark.parametrize("threshold", [0, 1, 3, 10, 100000])
 def test_votes_match_oracle(threshold, engine):
     seed = 77
