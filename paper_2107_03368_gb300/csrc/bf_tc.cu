@@ -10,32 +10,35 @@
 // exact.  The epilogue turns O into the Eq. 1 key (A = |q| - O, B = |t| - O)
 // and keeps per-query top-k.
 //
-// Kernel organisation (one persistent CTA per SM, 17 warps).  A work unit
-// is two 128-query tiles against a run of 128-descriptor tiles, so every
-// widened database chunk feeds the MMAs of 256 queries:
-//   * warps 8-15 (producers, half a database row per thread): for each
-//     128-bit K chunk, widen the chunk of 128 database descriptors into a
-//     16 KB shared-memory stage (K-major 8x16-byte core matrices); each
-//     thread loads its next four half-chunks (32 bytes) while it widens the
-//     current ones and sums its half row's |t| into shared memory.  The
-//     first lane of warp 8 also brings the matching 16 KB chunks of the two
-//     pre-widened query tiles with bulk copies (TMA engine);
-//   * warp 16 (one thread): per chunk and query tile, 4 MMAs of
-//     128 x 128 x 32 into that tile's half of one of two TMEM accumulators
-//     (256 columns each), then commits to free the stage;
-//   * warps 0-7 (epilogue, one thread per query row = TMEM lane; warps 0-3
-//     serve the first query tile, 4-7 the second): read the finished
-//     accumulator in 32-column slices while the next tile is being
-//     multiplied into the other accumulator, rank candidates, keep top-k.
-//     A slice is first tested as a whole: from its largest overlap and the
-//     smallest |t| of its 32 rows (a warp minimum taken by the producers)
-//     follows a lower bound on every key in it, and when that bound exceeds
-//     the query's k-th key the slice is skipped — almost every slice, once
-//     the list holds near neighbours.
-// A four-stage mbarrier ring connects producers and MMA; all waits are
-// bounded and a shared abort flag makes every role leave together.  Work
-// units are (pair of query tiles, database split), or come from a unit
-// table (list mode); per-split lists are merged afterwards.
+// Kernel organisation (one persistent CTA per SM).  A work unit is one
+// 128-query tile against a run of 128-descriptor database tiles, taken two
+// tiles (256 rows) per step, so every MMA is 128 x 256 x 32: per byte the
+// tensor cores read from shared memory it does half again the work of a
+// 128 x 128 MMA, and operand reads from shared memory are what bound the
+// tensor pipe here.  Units come in pairs of query tiles (split mode: the
+// pair's tiles scan the same database split on neighbouring CTAs, which
+// share the database chunks in L2).  Per 128-bit K chunk a 48 KB stage
+// holds the chunk of the query tile and of both database tiles, 128-byte
+// swizzled:
+//   * database chunks come either pre-widened (one copy of the database as
+//     E4M3 stage images, made once per call; a single thread brings each
+//     stage in with bulk copies, TMA engine) or are widened in the kernel
+//     by 8 producer warps, one database row of the step per thread, which
+//     sum |t| on the way; the query tiles are always pre-widened;
+//   * one thread issues, per chunk, 4 MMAs of 128 x 256 x 32 into one of
+//     two 256-column TMEM accumulators, then commits to free the stage;
+//   * the epilogue warps (one thread per query row = TMEM lane, each warp a
+//     group of 32-column slices) read the finished accumulator while the
+//     next step is multiplied into the other one, and keep top-k.  A slice
+//     is first tested as a whole: from its largest overlap and the smallest
+//     |t| of its 32 rows follows a lower bound on every key in it, and when
+//     that bound exceeds the query's k-th key the slice is skipped.
+//     Otherwise every row's key is compared without branches and only the
+//     rows that qualify are inserted.
+// A four-stage mbarrier ring connects copies/producers and MMA; all waits
+// are bounded and a shared abort flag makes every role leave together.
+// Work units are (query tile, database split), or come from a unit table
+// (list mode); per-split lists are merged afterwards.
 #include <algorithm>
 #include <mutex>
 
@@ -46,29 +49,33 @@ namespace dtk {
 namespace {
 
 constexpr int TM = 128;                 // queries per tile (MMA M)
-constexpr int QT = 2;                   // query tiles per unit
-constexpr int TN = 128;                 // descriptors per tile (MMA N)
+constexpr int QT = 2;                   // query tiles per unit pair
+constexpr int TN = 128;                 // descriptors per database tile
+constexpr int NB = 2;                   // database tiles per step
+constexpr int BN = NB * TN;             // descriptors per step (MMA N)
 constexpr int KC = 128;                 // K bytes (= bits) per chunk
 constexpr int NCHUNK = kBits / KC;      // 32
 constexpr int STAGES = 4;
-constexpr int A_STAGE = TM * KC;        // 16 KB per query tile
-constexpr int B_STAGE = TN * KC;        // 16 KB
-constexpr int STAGE = QT * A_STAGE + B_STAGE;   // 48 KB
-constexpr uint32_t LBO = 128;           // next core matrix along K
-constexpr uint32_t SBO = (KC / 16) * 128;  // next 8-row group (1024 B)
-constexpr int EPI_WARPS = 8, PROD_WARPS = 8;    // producers: two per database row
+constexpr int A_STAGE = TM * KC;        // 16 KB: the query tile's chunk
+constexpr int B_STAGE = TN * KC;        // 16 KB per database tile
+constexpr int STAGE = A_STAGE + NB * B_STAGE;   // 48 KB
+constexpr uint32_t SBO = 8 * KC;        // next 8-row atom (1 KB)
+constexpr int SLICES = BN / 32;         // 32-column slices of an accumulator
+constexpr int EPI_WARPS = 8, PROD_WARPS = BN / 32;   // producers: one database row per thread
 // Warp roles.  In-kernel widening: epilogue 0-7, producers 8-15, MMA 16.
-// Pre-widened database (PRE): epilogue 0-15, copy issuer 16, MMA 17; each
-// epilogue warp then covers half of its tile's columns, so a query ends a
-// unit with one sorted list per half.
+// Pre-widened database (PRE): epilogue 0-15, copy issuer 16, MMA 17.
+// Epilogue warp w reads TMEM lanes 32 (w % 4) .. + 31 and the slices of
+// group w / 4; a query ends a unit with one sorted list per group (split
+// mode), or all slices go to group 0 (list mode: one list per slot).
 __host__ __device__ constexpr int epi_warps(bool pre) { return pre ? 2 * EPI_WARPS : EPI_WARPS; }
 __host__ __device__ constexpr int mma_warp(bool pre) { return pre ? 17 : 16; }
 __host__ __device__ constexpr int kernel_threads(bool pre) { return (mma_warp(pre) + 1) * 32; }
-__host__ __device__ constexpr int lists_per_unit(bool pre) { return pre ? 2 : 1; }
-constexpr uint32_t ACC_COLS = QT * TN;  // one accumulator: 128 columns per query tile
+__host__ __device__ constexpr int lists_per_unit(bool pre) { return epi_warps(pre) / 4; }
+constexpr uint32_t ACC_COLS = BN;       // one accumulator: 256 columns
 constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;    // double-buffered: 512
-constexpr uint32_t IDESC = idesc_e4m3_f32(TM, TN);
-static_assert(TN == 4 * 32 && PROD_WARPS == 2 * (TN / 32), "two producer warps per 32 rows");
+constexpr uint32_t IDESC = idesc_e4m3_f32(TM, BN);
+static_assert(PROD_WARPS == 8 && TN % 32 == 0, "one producer thread per row of a step");
+static_assert(SLICES % lists_per_unit(true) == 0, "slices split evenly over the groups");
 
 struct TcCtl {
     uint64_t full[STAGES];
@@ -87,27 +94,26 @@ constexpr size_t STAGE_BYTES = (size_t)STAGES * STAGE;
 // carries none of the others' code.
 enum { MODE_PLAIN = 0, MODE_TREE = 1, MODE_BOUND = 2 };
 
-// |t| of the rows of the last tp_ring(MODE) tiles: producers write a tile's
-// |t| at its last chunk and the epilogue reads it once the tile's
-// accumulator is full.  With whole 32-chunk tiles the producers can be at
-// most one tile past the slowest epilogue warp's other buffer, so two
-// entries do.  With K chunks skipped (tree mode) a tile can be a single
-// chunk: the producers can then finish up to STAGES tiles past the one the
-// MMA waits to start, which is two past the slowest epilogue warp's, so
-// STAGES + 2 entries are in use at most.
-__host__ __device__ constexpr int tp_ring(int mode) { return mode == MODE_TREE ? 8 : 2; }
-static_assert(tp_ring(MODE_TREE) >= STAGES + 2, "|t| ring of the tree mode");
-// One ring entry per tile, contiguous so that a single bulk copy can fill
-// it: |t| of every row as two half-row sums [2][TN], then the smallest half
-// sum of each 32 rows [2][TN / 32] (uint32 throughout).  The pre-widened
-// database keeps one such record per tile (whole |t| in the first half,
-// zeros in the second).
-constexpr int SIDE_WORDS = 2 * TN + 2 * (TN / 32);
-constexpr uint32_t SIDE_BYTES = SIDE_WORDS * 4;          // 1,056
+// |t| of the rows of the last tp_ring(MODE) steps: the copy issuer or the
+// producers write a step's records with its last chunk and the epilogue
+// reads them once the step's accumulator is full.  The copies run at most
+// STAGES chunks ahead of the MMAs, which run at most one step ahead of the
+// slowest epilogue warp (two accumulators).  With whole 32-chunk steps the
+// next step's records can be written while the epilogue reads, the one
+// after only once the epilogue is done: two entries.  With K chunks skipped
+// (tree mode) a step can be a single chunk, so the records of up to
+// STAGES + 1 later steps can be written meanwhile: STAGES + 2 entries.
+__host__ __device__ constexpr int tp_ring(int mode) { return mode == MODE_TREE ? STAGES + 2 : 2; }
+// One record per database tile, contiguous so that a single bulk copy can
+// fill it: |t| of every row [TN], then the smallest |t| of each 32 rows
+// [TN / 32] (uint32 throughout).  A ring entry holds the NB records of a
+// step.
+constexpr int SIDE_WORDS = TN + TN / 32;
+constexpr uint32_t SIDE_BYTES = SIDE_WORDS * 4;          // 528
 static_assert(SIDE_BYTES % 16 == 0, "bulk copies move multiples of 16 bytes");
 __host__ __device__ constexpr size_t smem_bytes(int mode)
 {
-    return STAGE_BYTES + sizeof(TcCtl) + (size_t)tp_ring(mode) * SIDE_BYTES + 1024;
+    return STAGE_BYTES + sizeof(TcCtl) + (size_t)tp_ring(mode) * NB * SIDE_BYTES + 1024;
 }
 
 __device__ uint32_t g_tc_error;  // a bounded wait gave up (DT_ETIMEOUT)
@@ -131,10 +137,14 @@ __device__ __forceinline__ void widen32(uint32_t w, uint4 &lo, uint4 &hi)
                     bitplane_e4m3(w, 7));
 }
 
-// Byte offset of (row, 16-byte piece j of the chunk) in a K-major stage.
+// Byte offset of (row, 16-byte piece j of the chunk) in a K-major stage
+// with the 128-byte swizzle: row r of 128 bytes in the 1 KB atom r / 8,
+// piece j at position j ^ (r % 8) of the row.  The eight rows of an atom
+// written by eight threads for the same j fall in eight different bank
+// groups.
 __device__ __forceinline__ uint32_t core_off(int row, int j)
 {
-    return (uint32_t)(row >> 3) * SBO + (uint32_t)j * LBO + (uint32_t)(row & 7) * 16u;
+    return (uint32_t)(row >> 3) * SBO + (uint32_t)(row & 7) * KC + (uint32_t)((j ^ (row & 7)) * 16);
 }
 
 // Write 128 bits of one row as 128 E4M3 bytes into a stage.
@@ -148,18 +158,6 @@ __device__ __forceinline__ void store_row_chunk(unsigned char *stage, int row, u
         *reinterpret_cast<uint4 *>(stage + core_off(row, 2 * i)) = lo;
         *reinterpret_cast<uint4 *>(stage + core_off(row, 2 * i + 1)) = hi;
     }
-}
-
-// Write 64 bits (half hw of a 128-bit chunk) of one row: pieces 4 hw .. 4 hw + 3.
-__device__ __forceinline__ void store_half_chunk(unsigned char *stage, int row, int hw, uint2 bits)
-{
-    uint4 lo, hi;
-    widen32(bits.x, lo, hi);
-    *reinterpret_cast<uint4 *>(stage + core_off(row, 4 * hw)) = lo;
-    *reinterpret_cast<uint4 *>(stage + core_off(row, 4 * hw + 1)) = hi;
-    widen32(bits.y, lo, hi);
-    *reinterpret_cast<uint4 *>(stage + core_off(row, 4 * hw + 2)) = lo;
-    *reinterpret_cast<uint4 *>(stage + core_off(row, 4 * hw + 3)) = hi;
 }
 
 // Queries -> pre-widened tiles a_exp[m_tile][chunk][16 KB stage image], plus |q|.
@@ -227,12 +225,8 @@ __global__ void side_kernel(const uint32_t *__restrict__ rowpop, int64_t n,
     const uint32_t v = i < n ? rowpop[i] : 0u;
     uint32_t *e = side + t * SIDE_WORDS;
     e[row] = v;
-    e[TN + row] = 0u;
     const uint32_t mn = __reduce_min_sync(0xffffffffu, v);
-    if (lane == 0) {
-        e[2 * TN + w] = mn;
-        e[2 * TN + TN / 32 + w] = 0u;
-    }
+    if (lane == 0) e[TN + w] = mn;
 }
 
 // Bounded wait that also gives up when another role aborted.  The thread
@@ -273,9 +267,10 @@ struct TcArgs {
     int64_t n_ntiles;
     int64_t tiles_per_split;
     int n_split;
-    // Unit table (list mode): when non-null, unit u is units[u] and the
-    // unit count is read from *n_units; otherwise units are (query tile,
-    // database split) pairs of the whole database.
+    // Unit table (list mode): when non-null, units[u] gives the pair of
+    // query tiles 2u, 2u + 1 and the pair count is read from *n_units;
+    // otherwise units are (query tile, database split) over the whole
+    // database, the two tiles of a pair next to each other.
     const TcUnit *units;
     const int64_t *n_units;
     uint64_t *partial;               // split mode: [n_split][nq][k]; list mode: [slot][k]
@@ -302,56 +297,54 @@ struct TcArgs {
     const uint32_t *b_side;
 };
 
-// One work unit: query tiles mt[0], mt[1] (mt[1] < 0: absent) against
-// database rows [r0, r1), taken in tiles of TN rows from r0; query rows
-// >= nvalid[i] of tile i are padding.
+// One work unit: query tile mt (< 0: absent, no tiles) against database
+// rows [r0, r1), taken in tiles of TN rows from r0 and multiplied NB tiles
+// per step; query rows >= nvalid are padding.  Unit u is query tile u % 2
+// of pair unit u / 2.
 struct Unit {
-    int64_t mt[QT];
+    int64_t mt;
     int64_t r0, r1, ntiles, sp, out_base;
     int64_t mp, t0;                  // split mode: query-tile pair, first global tile
-    int nvalid[QT];
+    int nvalid;
 };
 
 __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
 {
     Unit v;
+    const int64_t pu = u >> 1;
+    const int qh = (int)(u & 1);
     if (a.units) {
-        const TcUnit t = a.units[u];
-        v.mt[0] = t.a_tile0;
-        v.mt[1] = t.a_tile1;
+        const TcUnit t = a.units[pu];
+        v.mt = qh ? t.a_tile1 : t.a_tile0;
+        v.nvalid = qh ? t.nvalid1 : t.nvalid0;
         v.r0 = t.row0;
         v.r1 = t.row1;
-        v.ntiles = (t.row1 - t.row0 + TN - 1) / TN;
         v.sp = 0;
         v.mp = 0;
         v.t0 = 0;
         v.out_base = t.out_base;
-        v.nvalid[0] = t.nvalid0;
-        v.nvalid[1] = t.a_tile1 >= 0 ? t.nvalid1 : 0;
     } else {
-        const int64_t mp = a.mp_base + u % a.n_mpairs;
-        v.sp = u / a.n_mpairs;
+        const int64_t mp = a.mp_base + pu % a.n_mpairs;
+        v.sp = pu / a.n_mpairs;
         v.mp = mp;
         v.out_base = 0;
         const int64_t t0 = v.sp * a.tiles_per_split;
         v.t0 = t0;
-        const int64_t t1 = min(a.n_ntiles, t0 + a.tiles_per_split);
         v.r0 = t0 * TN;
         v.r1 = a.n;
-        v.ntiles = t1 - t0;
-#pragma unroll
-        for (int i = 0; i < QT; ++i) {
-            const int64_t mt = QT * mp + i;
-            v.mt[i] = mt < a.n_mtiles ? mt : -1;
-            v.nvalid[i] = mt < a.n_mtiles ? (int)min((int64_t)TM, a.nq - mt * TM) : 0;
-        }
+        const int64_t mt = QT * mp + qh;
+        v.mt = mt < a.n_mtiles ? mt : -1;
+        v.nvalid = mt < a.n_mtiles ? (int)min((int64_t)TM, a.nq - mt * TM) : 0;
     }
+    if (v.mt < 0) v.ntiles = 0;
+    else if (a.units) v.ntiles = (v.r1 - v.r0 + TN - 1) / TN;
+    else v.ntiles = min(a.n_ntiles, v.t0 + a.tiles_per_split) - v.t0;
     return v;
 }
 
 __device__ __forceinline__ int64_t unit_count(const TcArgs &a)
 {
-    return a.units ? *a.n_units : (int64_t)a.n_mpairs * a.n_split;
+    return 2 * (a.units ? *a.n_units : (int64_t)a.n_mpairs * a.n_split);
 }
 
 // The first tile at or after local tile lt of unit uv that is multiplied
@@ -383,6 +376,39 @@ __device__ __forceinline__ uint32_t chunk_mask(const TcArgs &a, const Unit &uv, 
     return m ? m : 1u;
 }
 
+// A step: local tiles lt[0] and lt[1] of a unit (lt[1] < 0: absent), the
+// two halves of one 256-row MMA operand.  The first step at or after local
+// tile `from` pairs the next two tiles that are multiplied (adjacent ones
+// without a need bitmap); lt[0] == uv.ntiles when none is left.
+struct Step {
+    int64_t lt[NB];
+};
+
+template <int MODE>
+__device__ __forceinline__ Step first_step(const TcArgs &a, const Unit &uv, int64_t from)
+{
+    Step st;
+    st.lt[0] = next_tile<MODE>(a, uv, from);
+    const int64_t l1 = st.lt[0] < uv.ntiles ? next_tile<MODE>(a, uv, st.lt[0] + 1) : uv.ntiles;
+    st.lt[1] = l1 < uv.ntiles ? l1 : -1;
+    return st;
+}
+
+// Local tile after the step: where the next step's search starts.
+__device__ __forceinline__ int64_t step_end(const Step &st)
+{
+    return (st.lt[1] >= 0 ? st.lt[1] : st.lt[0]) + 1;
+}
+
+// K chunks multiplied in a step: those of either tile.
+template <int MODE>
+__device__ __forceinline__ uint32_t step_mask(const TcArgs &a, const Unit &uv, const Step &st)
+{
+    uint32_t m = chunk_mask<MODE>(a, uv, st.lt[0]);
+    if (st.lt[1] >= 0) m |= chunk_mask<MODE>(a, uv, st.lt[1]);
+    return m;
+}
+
 // The first unit at or after u (in steps of the grid) with a tile to multiply.
 template <int MODE>
 __device__ __forceinline__ int64_t next_busy(const TcArgs &a, int64_t u, int64_t total, Unit &uv)
@@ -394,14 +420,14 @@ __device__ __forceinline__ int64_t next_busy(const TcArgs &a, int64_t u, int64_t
     return u;
 }
 
-// 8 bytes (half hw of chunk c) of row `row` of tile lt of unit uv, zeros
-// past its end.
-__device__ __forceinline__ uint2 load_half(const TcArgs &a, const Unit &uv, int64_t lt, int row,
-                                           int hw, int c)
+// Chunk c (16 bytes) of row `row` of local tile lt of unit uv; zeros past
+// the unit's rows or for an absent tile (lt < 0).
+__device__ __forceinline__ uint4 load_row(const TcArgs &a, const Unit &uv, int64_t lt, int row, int c)
 {
+    if (lt < 0) return make_uint4(0, 0, 0, 0);
     const int64_t t = uv.r0 + lt * TN + row;
-    if (t >= uv.r1) return make_uint2(0, 0);
-    return __ldg(reinterpret_cast<const uint2 *>(a.db + t * kWords) + 2 * c + hw);
+    if (t >= uv.r1) return make_uint4(0, 0, 0, 0);
+    return __ldg(reinterpret_cast<const uint4 *>(a.db + t * kWords) + c);
 }
 
 // Insert a candidate into a thread's sorted top-k list (rare once the list
@@ -428,16 +454,19 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         ((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *stageA = smem;                                   // [STAGES][QT][A_STAGE]
-    unsigned char *stageB = smem + (size_t)STAGES * QT * A_STAGE;   // [STAGES][B_STAGE]
+    // stage s: the query tile's chunk [A_STAGE], then the step's database
+    // tiles' chunks [NB][B_STAGE] (rows 0-127 and 128-255 of the operand)
     TcCtl *ctl = reinterpret_cast<TcCtl *>(smem + STAGE_BYTES);
-    // |t| ring: entry tile % TP_RING (SIDE_WORDS words, layout above)
+    // |t| ring: entry step % TP_RING (NB records of SIDE_WORDS words)
     static_assert(sizeof(TcCtl) % 16 == 0, "ring entries start 16-byte aligned");
     uint32_t *ring = reinterpret_cast<uint32_t *>(smem + STAGE_BYTES + sizeof(TcCtl));
     constexpr int TP_RING = tp_ring(MODE);
     uint32_t *err = args.err;
 
-    constexpr int EPI = epi_warps(PRE), MMAW = mma_warp(PRE), NL = lists_per_unit(PRE);
+    constexpr int EPI = epi_warps(PRE), MMAW = mma_warp(PRE);
+    // slice groups: one per 4 epilogue warps in split mode, a single one
+    // (one list per slot) in list mode
+    const int ngroups = args.units ? 1 : EPI / 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -447,7 +476,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&ctl->acc_full[a], 1);
-            mbar_init(&ctl->acc_empty[a], EPI);
+            mbar_init(&ctl->acc_empty[a], 4 * ngroups);
         }
         mbar_init(&ctl->final_bar, 1);
         ctl->abort = 0u;
@@ -467,40 +496,47 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
     if (PRE && warp == EPI) {
         // ------------------------------------------------ copy issuer (PRE)
         // The database arrives widened: one thread issues, per chunk, the
-        // query tiles' chunks and the database tile's chunk, and with a
-        // tile's last chunk the tile's |t| record into the ring (at the same
-        // point of the sequence where the producers below write it).
+        // query tile's chunk and the chunks of the step's database tiles,
+        // and with a step's last chunk the tiles' |t| records into the ring
+        // (at the same point of the sequence where the producers below
+        // write them).
         if (lane == 0) {
-            uint32_t g = 0, tile = 0;
+            uint32_t g = 0, t = 0;
+            // query tiles are read again for every database tile: kept in
+            // L2; the widened database streams past once per CTA wave
+            const uint64_t keep = l2_keep_policy(), stream = l2_stream_policy();
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
                 const Unit uv = get_unit(args, u);
-                const int64_t mt0 = uv.mt[0], mt1 = uv.mt[1];
-                for (int64_t lt = next_tile<MODE>(args, uv, 0); lt < uv.ntiles;
-                     lt = next_tile<MODE>(args, uv, lt + 1)) {
-                    const int64_t gt = uv.t0 + lt;
-                    const uint32_t km = chunk_mask<MODE>(args, uv, lt);
+                for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
+                     st = first_step<MODE>(args, uv, step_end(st)), ++t) {
+                    const int64_t gt0 = uv.t0 + st.lt[0];
+                    const int64_t gt1 = st.lt[1] >= 0 ? uv.t0 + st.lt[1] : -1;
+                    const uint32_t km = step_mask<MODE>(args, uv, st);
                     const int last_c = 31 - __clz(km);
+                    const uint32_t nb = gt1 >= 0 ? 2u : 1u;
+                    uint32_t *slot = ring + (t % TP_RING) * (NB * SIDE_WORDS);
                     for (uint32_t m = km; m; m &= m - 1, ++g) {
                         const int c = __ffs(m) - 1;
                         const int s = (int)(g % STAGES);
                         const uint32_t r = g / STAGES;
                         if (!wait_or_abort(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err)) goto done;
-                        const uint32_t bytes = (mt1 >= 0 ? 2u : 1u) * A_STAGE + B_STAGE +
-                                               (c == last_c ? SIDE_BYTES : 0u);
+                        const uint32_t bytes = A_STAGE + nb * B_STAGE + (c == last_c ? nb * SIDE_BYTES : 0u);
                         mbar_arrive_expect_tx(&ctl->full[s], bytes);
-                        unsigned char *a_dst = stageA + (size_t)s * QT * A_STAGE;
-                        bulk_g2s(a_dst, args.a_exp + ((size_t)mt0 * NCHUNK + c) * A_STAGE,
-                                 (uint32_t)A_STAGE, &ctl->full[s]);
-                        if (mt1 >= 0)
-                            bulk_g2s(a_dst + A_STAGE, args.a_exp + ((size_t)mt1 * NCHUNK + c) * A_STAGE,
-                                     (uint32_t)A_STAGE, &ctl->full[s]);
-                        bulk_g2s(stageB + (size_t)s * B_STAGE,
-                                 args.b_exp + ((size_t)gt * NCHUNK + c) * B_STAGE, (uint32_t)B_STAGE,
-                                 &ctl->full[s]);
+                        unsigned char *dst = smem + (size_t)s * STAGE;
+                        bulk_g2s_hint(dst, args.a_exp + ((size_t)uv.mt * NCHUNK + c) * A_STAGE,
+                                      (uint32_t)A_STAGE, &ctl->full[s], keep);
+                        bulk_g2s_hint(dst + A_STAGE, args.b_exp + ((size_t)gt0 * NCHUNK + c) * B_STAGE,
+                                      (uint32_t)B_STAGE, &ctl->full[s], stream);
+                        if (gt1 >= 0)
+                            bulk_g2s_hint(dst + A_STAGE + B_STAGE,
+                                          args.b_exp + ((size_t)gt1 * NCHUNK + c) * B_STAGE,
+                                          (uint32_t)B_STAGE, &ctl->full[s], stream);
                         if (c == last_c) {
-                            bulk_g2s(ring + (tile & (TP_RING - 1)) * SIDE_WORDS,
-                                     args.b_side + (size_t)gt * SIDE_WORDS, SIDE_BYTES, &ctl->full[s]);
-                            ++tile;
+                            bulk_g2s_hint(slot, args.b_side + (size_t)gt0 * SIDE_WORDS, SIDE_BYTES,
+                                          &ctl->full[s], stream);
+                            if (gt1 >= 0)
+                                bulk_g2s_hint(slot + SIDE_WORDS, args.b_side + (size_t)gt1 * SIDE_WORDS,
+                                              SIDE_BYTES, &ctl->full[s], stream);
                         }
                     }
                 }
@@ -508,20 +544,20 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         }
     } else if (!PRE && warp >= EPI_WARPS && warp < EPI_WARPS + PROD_WARPS) {
         // ------------------------------------------------ producers
-        // Half a database row per thread (warps 8-11 the first 8 bytes of each
-        // chunk, warps 12-15 the second).  Chunks are visited in groups of
-        // four consecutive chunk indices; a group is loaded (32 bytes a
-        // thread) one group ahead of the one being widened, and only the
-        // chunks of the tile's mask are widened and handed to the MMA.  |t|
-        // is summed on the way (skipped chunks hold no bit of any row of the
-        // tile) and left in shared memory for the epilogue.
-        const int pw = warp - EPI_WARPS;
-        const int rg = pw & 3, hw = pw >> 2;
-        const int row = rg * 32 + lane;
+        // One database row of the step per thread: warps 8-11 the rows of
+        // the step's first tile, 12-15 those of its second.  Chunks are
+        // visited in groups of four consecutive chunk indices; a group is
+        // loaded (64 bytes a thread) one group ahead of the one being
+        // widened, and only the chunks of the step's mask are widened and
+        // handed to the MMA.  |t| is summed on the way (skipped chunks hold
+        // no bit of any row of either tile) and left in the ring.
+        const int p = (warp - EPI_WARPS) * 32 + lane;   // row of the 256-row operand
+        const int h = p / TN, row = p % TN, rg = row / 32;
         constexpr int G = 4;                       // chunks per load group
-        uint32_t g = 0, tile = 0, tp_acc = 0;
+        uint32_t g = 0, t = 0, tp_acc = 0;
         Unit uv{};
-        int64_t u = next_busy<MODE>(args, blockIdx.x, total_units, uv), lt = 0;
+        int64_t u = next_busy<MODE>(args, blockIdx.x, total_units, uv);
+        Step st{};
         uint32_t km = 0;
         int grp = 0;
         // first group of the mask at or after group gi, or NCHUNK / G
@@ -531,39 +567,40 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
             return rest ? gi + (__ffs(rest) - 1) / G : NCHUNK / G;
         };
         if (u < total_units) {
-            lt = next_tile<MODE>(args, uv, 0);
-            km = chunk_mask<MODE>(args, uv, lt);
+            st = first_step<MODE>(args, uv, 0);
+            km = step_mask<MODE>(args, uv, st);
             grp = first_group(km, 0);
         }
-        uint2 nx[G];
+        uint4 nx[G];
 #pragma unroll
         for (int i = 0; i < G; ++i)
-            nx[i] = u < total_units ? load_half(args, uv, lt, row, hw, grp * G + i) : make_uint2(0, 0);
+            nx[i] = u < total_units ? load_row(args, uv, st.lt[h], row, grp * G + i)
+                                    : make_uint4(0, 0, 0, 0);
         while (u < total_units) {
-            const int64_t mt0 = uv.mt[0], mt1 = uv.mt[1];
+            const int64_t mt = uv.mt;
             const int cur_grp = grp;
             const uint32_t cur_km = km;
             const int last_c = MODE == MODE_TREE ? 31 - __clz(cur_km) : NCHUNK - 1;
-            uint2 cu[G];
+            uint4 cu[G];
 #pragma unroll
             for (int i = 0; i < G; ++i) cu[i] = nx[i];
-            // advance (u, lt, grp) to the next group with a chunk to multiply
-            // and prefetch it
+            // advance (u, step, grp) to the next group with a chunk to
+            // multiply and prefetch it
             grp = first_group(km, grp + 1);
             if (grp == NCHUNK / G) {
-                lt = next_tile<MODE>(args, uv, lt + 1);
-                if (lt == uv.ntiles) {
+                st = first_step<MODE>(args, uv, step_end(st));
+                if (st.lt[0] == uv.ntiles) {
                     u = next_busy<MODE>(args, u + gridDim.x, total_units, uv);
-                    lt = u < total_units ? next_tile<MODE>(args, uv, 0) : 0;
+                    if (u < total_units) st = first_step<MODE>(args, uv, 0);
                 }
                 if (u < total_units) {
-                    km = chunk_mask<MODE>(args, uv, lt);
+                    km = step_mask<MODE>(args, uv, st);
                     grp = first_group(km, 0);
                 }
             }
             if (u < total_units) {
 #pragma unroll
-                for (int i = 0; i < G; ++i) nx[i] = load_half(args, uv, lt, row, hw, grp * G + i);
+                for (int i = 0; i < G; ++i) nx[i] = load_row(args, uv, st.lt[h], row, grp * G + i);
             }
 #pragma unroll
             for (int i = 0; i < G; ++i) {
@@ -572,25 +609,21 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                 const int s = (int)(g % STAGES);
                 const uint32_t r = g / STAGES;
                 if (!warp_wait(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err, lane)) goto done;
-                if (pw == 0 && lane == 0) {
-                    unsigned char *a_dst = stageA + (size_t)s * QT * A_STAGE;
-                    mbar_arrive_expect_tx(&ctl->full[s], (uint32_t)(mt1 >= 0 ? 2 : 1) * A_STAGE);
-                    bulk_g2s(a_dst, args.a_exp + ((size_t)mt0 * NCHUNK + c) * A_STAGE,
+                unsigned char *dst = smem + (size_t)s * STAGE;
+                if (p == 0) {
+                    mbar_arrive_expect_tx(&ctl->full[s], (uint32_t)A_STAGE);
+                    bulk_g2s(dst, args.a_exp + ((size_t)mt * NCHUNK + c) * A_STAGE,
                              (uint32_t)A_STAGE, &ctl->full[s]);
-                    if (mt1 >= 0)
-                        bulk_g2s(a_dst + A_STAGE, args.a_exp + ((size_t)mt1 * NCHUNK + c) * A_STAGE,
-                                 (uint32_t)A_STAGE, &ctl->full[s]);
                 }
-                store_half_chunk(stageB + (size_t)s * B_STAGE, row, hw, cu[i]);
-                tp_acc += __popc(cu[i].x) + __popc(cu[i].y);
-                if (c == last_c) {                     // half row complete: |t| part for the epilogue
-                    const uint32_t tr = tile & (TP_RING - 1);
-                    uint32_t *e = ring + tr * SIDE_WORDS;
-                    e[hw * TN + row] = tp_acc;
+                store_row_chunk(dst + A_STAGE, p, cu[i]);
+                tp_acc += __popc(cu[i].x) + __popc(cu[i].y) + __popc(cu[i].z) + __popc(cu[i].w);
+                if (c == last_c) {                     // row complete: its record for the epilogue
+                    uint32_t *e = ring + (t % TP_RING) * (NB * SIDE_WORDS) + h * SIDE_WORDS;
+                    e[row] = tp_acc;
                     const uint32_t mn = __reduce_min_sync(0xffffffffu, tp_acc);
-                    if (lane == 0) e[2 * TN + hw * (TN / 32) + rg] = mn;
+                    if (lane == 0) e[TN + rg] = mn;
                     tp_acc = 0;
-                    ++tile;
+                    ++t;
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
@@ -604,32 +637,26 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
             uint32_t g = 0, t = 0;
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
                 const Unit uv = get_unit(args, u);
-                for (int64_t lt = next_tile<MODE>(args, uv, 0); lt < uv.ntiles;
-                     lt = next_tile<MODE>(args, uv, lt + 1), ++t) {
+                for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
+                     st = first_step<MODE>(args, uv, step_end(st)), ++t) {
                     const uint32_t acc = t & 1u, ra = t >> 1;
                     if (!wait_or_abort(&ctl->acc_empty[acc], (ra & 1u) ^ 1u, ctl, err)) goto mma_done;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + acc * ACC_COLS;
-                    const int n_qt = uv.mt[1] >= 0 ? 2 : 1;
-                    uint32_t km = chunk_mask<MODE>(args, uv, lt);
+                    uint32_t km = step_mask<MODE>(args, uv, st);
                     bool first = true;
                     for (; km; km &= km - 1, ++g) {
                         const int s = (int)(g % STAGES);
                         const uint32_t r = g / STAGES;
                         if (!wait_or_abort(&ctl->full[s], r & 1u, ctl, err)) goto mma_done;
                         tc_fence_after();
-                        const uint32_t a_base = smem_u32(stageA + (size_t)s * QT * A_STAGE);
-                        const uint32_t b_base = smem_u32(stageB + (size_t)s * B_STAGE);
-                        for (int i = 0; i < n_qt; ++i) {
+                        const uint32_t a_base = smem_u32(smem + (size_t)s * STAGE);
+                        const uint32_t b_base = a_base + A_STAGE;
 #pragma unroll
-                            for (int kk = 0; kk < KC / 32; ++kk) {
-                                const uint64_t ad = smem_desc_kmajor(
-                                    a_base + (uint32_t)i * A_STAGE + kk * 2 * LBO, LBO, SBO);
-                                const uint64_t bd = smem_desc_kmajor(b_base + kk * 2 * LBO, LBO, SBO);
-                                mma_e4m3(d_tmem + (uint32_t)i * TN, ad, bd, IDESC,
-                                         (!first || kk != 0) ? 1u : 0u);
-                            }
-                        }
+                        for (int kk = 0; kk < KC / 32; ++kk)
+                            mma_e4m3(d_tmem, smem_desc_sw128(a_base + kk * 32u, SBO),
+                                     smem_desc_sw128(b_base + kk * 32u, SBO), IDESC,
+                                     (!first || kk != 0) ? 1u : 0u);
                         first = false;
                         mma_commit(&ctl->empty[s]);
                     }
@@ -641,13 +668,13 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
             wait_or_abort(&ctl->final_bar, 0u, ctl, err);
         }
         __syncwarp();
-    } else {
-        // ------------------------------------------------ epilogue (warps 0 .. EPI-1)
-        // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its sub-partition) of
-        // query tile (w / 4) % 2: all of that tile's 128 accumulator columns,
-        // or with PRE the half w / 8 of them (slices cb0 .. cb1 - 1).
-        const int quarter = warp & 3, qt = (warp >> 2) & 1, half = NL > 1 ? warp >> 3 : 0;
-        const int cb0 = half * (TN / 32 / NL), cb1 = cb0 + TN / 32 / NL;
+    } else if (warp < EPI && (warp >> 2) < ngroups) {
+        // ------------------------------------------------ epilogue
+        // Warp w reads TMEM lanes 32 (w % 4) .. + 31 (its sub-partition)
+        // and slices cs0 .. cs1 - 1 of each accumulator; slice cs covers
+        // rows 32 (cs % 4) .. + 31 of the step's tile cs / 4.
+        const int quarter = warp & 3, grp = warp >> 2;
+        const int cs0 = grp * (SLICES / ngroups), cs1 = cs0 + SLICES / ngroups;
         const int row = quarter * 32 + lane;         // TMEM lane = query row of the tile
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         const int k = args.k;
@@ -656,33 +683,39 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         uint32_t t = 0;
         for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x) {
             const Unit uv = get_unit(args, u);
-            const bool present = uv.mt[qt] >= 0;
-            const int64_t qi = uv.mt[qt] * TM + row;   // query (split mode) or pair slot (list mode)
-            const bool valid = present && row < uv.nvalid[qt];
+            const int64_t qi = uv.mt * TM + row;      // query (split mode) or pair slot (list mode)
+            const bool valid = uv.mt >= 0 && row < uv.nvalid;
             const QueryWeights w = query_weights(valid ? args.qpop[qi] : 0u);
             // a cap known to be >= the exact k-th key: nothing above it is kept
             const uint32_t capk =
                 (MODE != MODE_PLAIN && args.cap && valid) ? __ldg(args.cap + qi) : 0xFFFFFFFFu;
             const uint64_t capw = capk == 0xFFFFFFFFu ? kEmpty : pack(capk, 0xFFFFFFFFu);
-            // key = A*Z + B*P = (|q| - O) Z + (|t| - O) P = |t| P + |q| Z - O (Z + P)
+            // key = A*Z + B*P = (|q| - O) Z + (|t| - O) P = |t| P + |q| Z - O (Z + P).
+            // The bit pattern F of 4096 * sum + 2^23 is 0x4B000000 + O, so
+            // key = |t| P + (|q| Z + 0x4B000000 (Z + P)) - F (Z + P) in
+            // 32-bit arithmetic, which wraps back to the exact key.
             const uint32_t qz = w.pop * w.Z, zp = w.Z + w.P;
+            const uint32_t qzc = qz + 0x4B000000u * zp, nzp = 0u - zp;
             for (int j = 0; j < k; ++j) L[j] = kEmpty;
             uint64_t worst = capw;
             uint32_t wkey = capk;             // key part of `worst`
-            for (int64_t lt = next_tile<MODE>(args, uv, 0); lt < uv.ntiles;
-                 lt = next_tile<MODE>(args, uv, lt + 1), ++t) {
+            for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
+                 st = first_step<MODE>(args, uv, step_end(st)), ++t) {
                 const uint32_t acc = t & 1u, ra = t >> 1;
                 if (!warp_wait(&ctl->acc_full[acc], ra & 1u, ctl, err, lane)) goto done;
                 tc_fence_after();
-                const int64_t base = uv.r0 + lt * TN;
-                if constexpr (MODE == MODE_BOUND) {
-                    // bound pass: row j of the slice is the image of scan tile
-                    // base + 32 cb + j; a bit per tile some valid query may need
-                    for (int cb = cb0; cb < (present ? cb1 : cb0); ++cb) {
-                        uint32_t v[32];
-                        tmem_ld_32x32b_x32(lane_base + acc * ACC_COLS + (uint32_t)qt * TN + cb * 32, v);
-                        tmem_ld_wait();
-                        const int64_t b0 = base + cb * 32;
+                const uint32_t *side = ring + (t % TP_RING) * (NB * SIDE_WORDS);
+                for (int cs = cs0; cs < cs1; ++cs) {
+                    const int h = cs / (TN / 32), cb = cs % (TN / 32);
+                    const int64_t lt = st.lt[h];
+                    if (lt < 0) continue;
+                    const int64_t b0 = uv.r0 + lt * TN + cb * 32;
+                    uint32_t v[32];
+                    tmem_ld_32x32b_x32(lane_base + acc * ACC_COLS + (uint32_t)cs * 32, v);
+                    tmem_ld_wait();
+                    if constexpr (MODE == MODE_BOUND) {
+                        // bound pass: row j of the slice is the image of scan
+                        // tile b0 + j; a bit per tile some valid query may need
                         const int m = (int)(uv.r1 - b0 < 32 ? (uv.r1 - b0 > 0 ? uv.r1 - b0 : 0) : 32);
                         uint32_t bits = 0;
                         if (valid) {
@@ -698,19 +731,9 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                         bits = __reduce_or_sync(0xffffffffu, bits);
                         if (lane == 0 && bits)
                             atomicOr(args.need_out + uv.mp * args.need_words + (b0 >> 5), bits);
+                        continue;
                     }
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
-                    continue;
-                }
-                const uint32_t tr = t & (TP_RING - 1);
-                const uint32_t *tp0 = ring + tr * SIDE_WORDS, *tp1 = tp0 + TN;
-                const uint32_t *tm0 = tp0 + 2 * TN, *tm1 = tm0 + TN / 32;
-                for (int cb = cb0; cb < (present ? cb1 : cb0); ++cb) {
-                    uint32_t v[32];
-                    tmem_ld_32x32b_x32(lane_base + acc * ACC_COLS + (uint32_t)qt * TN + cb * 32, v);
-                    tmem_ld_wait();
+                    const uint32_t *tp = side + h * SIDE_WORDS;   // |t| [TN], minima [TN / 32]
                     // Slice filter: every key here is >= |t|min P + |q| Z - Omax (Z + P);
                     // when that exceeds the k-th key no row of the slice can enter
                     // the list.  The values are non-negative floats, ordered as
@@ -720,26 +743,37 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
 #pragma unroll
                         for (int j = 0; j < 32; j += 2) mx = __vimax3_u32(mx, v[j], v[j + 1]);
                         const uint32_t omax =
-                            __float_as_uint(fmaf(__uint_as_float(mx), 4096.0f, 8388608.0f)) -
-                            0x4B000000u;
-                        const uint32_t tmin = tm0[cb] + tm1[cb];   // <= min of the row sums
+                            __float_as_uint(fmaf(__uint_as_float(mx), 4096.0f, 8388608.0f)) - 0x4B000000u;
+                        const uint32_t tmin = tp[TN + cb];
                         if ((int64_t)omax * zp < (int64_t)qz + (int64_t)tmin * w.P - (int64_t)wkey)
                             continue;
                     }
-                    const int64_t b0 = base + cb * 32;
-                    const int m = (int)(uv.r1 - b0 < 32 ? uv.r1 - b0 : 32);
+                    // every row's key, without branches; v[j] becomes the key
+                    const uint4 *tp4 = reinterpret_cast<const uint4 *>(tp + cb * 32);
+                    uint32_t bits = 0;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        // sum = O * 2^-12 exactly: 4096 * sum + 2^23, read the mantissa
-                        const uint32_t o =
-                            __float_as_uint(fmaf(__uint_as_float(v[j]), 4096.0f, 8388608.0f)) -
-                            0x4B000000u;
-                        const uint32_t tpj = tp0[cb * 32 + j] + tp1[cb * 32 + j];
-                        const uint32_t key = tpj * w.P + qz - o * zp;
-                        if (j < m && key <= wkey) {   // rare once the list has filled
-                            worst = list_insert(L, k, key, b0 + j, args.idx_map, worst);
-                            if (MODE == MODE_TREE) worst = worst < capw ? worst : capw;
-                            wkey = (uint32_t)(worst >> 32);
+                    for (int j4 = 0; j4 < 8; ++j4) {
+                        const uint4 t4 = tp4[j4];
+                        const uint32_t tt[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const int j = 4 * j4 + i;
+                            const uint32_t f =
+                                __float_as_uint(fmaf(__uint_as_float(v[j]), 4096.0f, 8388608.0f));
+                            v[j] = f * nzp + (tt[i] * w.P + qzc);
+                            bits |= (v[j] <= wkey ? 1u : 0u) << j;
+                        }
+                    }
+                    const int64_t m = uv.r1 - b0;        // rows of the slice that exist
+                    if (m < 32) bits &= m > 0 ? (1u << m) - 1u : 0u;
+                    if (bits) {                          // rare once the list has filled
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if ((bits >> j) & 1u) {
+                                worst = list_insert(L, k, v[j], b0 + j, args.idx_map, worst);
+                                if (MODE == MODE_TREE) worst = worst < capw ? worst : capw;
+                                wkey = (uint32_t)(worst >> 32);
+                            }
                         }
                     }
                 }
@@ -748,9 +782,8 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                 if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
             }
             if (MODE != MODE_BOUND && valid) {
-                // (PRE kernels run in split mode only)
                 uint64_t *out = args.units ? args.partial + (uv.out_base + qi) * k
-                                           : args.partial + ((uv.sp * NL + half) * nq + qi) * k;
+                                           : args.partial + ((uv.sp * ngroups + grp) * nq + qi) * k;
                 for (int j = 0; j < k; ++j) out[j] = L[j];
             }
         }
@@ -805,6 +838,14 @@ bool want_prewiden(int64_t n, int64_t nq, int forced)
     return bytes <= free_b / 2;
 }
 
+// Tiles per split when n_tiles tiles are cut into `splits` splits, rounded
+// up to whole steps so that no split ends with a half-empty step.
+int64_t step_tiles(int64_t n_tiles, int splits)
+{
+    const int64_t t = (n_tiles + splits - 1) / splits;
+    return (t + NB - 1) / NB * NB;
+}
+
 // Stage images and |t| records of rows [0, n) of db, tiled by TN rows
 // (rows past n are zero), from `scratch`.
 int prewiden_rows(const uint64_t *db, int64_t n, Scratch &scratch, cudaStream_t s,
@@ -845,8 +886,8 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     const bool pre = want_prewiden(n, nq, c.b);
     const int batch_pairs = std::min(n_mpairs, kBatchPairs);
     const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_ntiles)
-                               : pick_bf_splits(batch_pairs, n_ntiles, sms);
-    const int64_t tiles_per_split = (n_ntiles + splits - 1) / splits;
+                               : pick_bf_splits(2 * batch_pairs, n_ntiles, sms);
+    const int64_t tiles_per_split = step_tiles(n_ntiles, splits);
     const int n_split = (int)((n_ntiles + tiles_per_split - 1) / tiles_per_split);
 
     unsigned char *a_exp = nullptr;
@@ -890,7 +931,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     for (int p0 = 0; p0 < n_mpairs; p0 += kBatchPairs) {     // L2-sized batches of queries
         a.mp_base = p0;
         a.n_mpairs = std::min(kBatchPairs, n_mpairs - p0);
-        const int grid = (int)std::min<int64_t>((int64_t)a.n_mpairs * n_split, sms);
+        const int grid = (int)std::min<int64_t>(2 * (int64_t)a.n_mpairs * n_split, sms);
         KernelTimer timer("tc_scan", s);
         if (pre)
             bf_tc_kernel<MODE_PLAIN, true><<<grid, kernel_threads(true), smem_bytes(MODE_PLAIN), s>>>(a);
@@ -983,7 +1024,7 @@ int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
     a.n_units = n_units;
     a.partial = partial;
     a.err = err;
-    const int grid = (int)std::min<int64_t>(max_units, sm_count());
+    const int grid = (int)std::min<int64_t>(2 * max_units, sm_count());
     bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
@@ -1030,8 +1071,8 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     b.n_ntiles = (n_tt + TN - 1) / TN;
     const int batch_pairs = std::min(n_mpairs, kBatchPairs);
     {
-        const int splits = pick_bf_splits(batch_pairs, b.n_ntiles, sms);
-        b.tiles_per_split = (b.n_ntiles + splits - 1) / splits;
+        const int splits = pick_bf_splits(2 * batch_pairs, b.n_ntiles, sms);
+        b.tiles_per_split = step_tiles(b.n_ntiles, splits);
         b.n_split = (int)((b.n_ntiles + b.tiles_per_split - 1) / b.tiles_per_split);
     }
     b.cap = cap_slot;
@@ -1042,7 +1083,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
         b.mp_base = p0;
         b.n_mpairs = std::min(kBatchPairs, n_mpairs - p0);
         KernelTimer timer("tree_bound", s);
-        bf_tc_kernel<MODE_BOUND, false><<<(int)std::min<int64_t>((int64_t)b.n_mpairs * b.n_split, sms),
+        bf_tc_kernel<MODE_BOUND, false><<<(int)std::min<int64_t>(2 * (int64_t)b.n_mpairs * b.n_split, sms),
                                            kernel_threads(false), smem_bytes(MODE_BOUND), s>>>(b);
     }
     DT_CUDA_TRY(cudaGetLastError());
@@ -1061,8 +1102,8 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     a.n_ntiles = n_tt;
     TuneCfg c{0, 0};
     tune_lookup(TUNE_TREE_TC, n, nq, k, &c);
-    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_tt) : pick_bf_splits(batch_pairs, n_tt, sms);
-    a.tiles_per_split = (n_tt + splits - 1) / splits;
+    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_tt) : pick_bf_splits(2 * batch_pairs, n_tt, sms);
+    a.tiles_per_split = step_tiles(n_tt, splits);
     a.n_split = (int)((n_tt + a.tiles_per_split - 1) / a.tiles_per_split);
     a.need = need;
     a.need_words = need_words;
@@ -1084,7 +1125,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     for (int p0 = 0; p0 < n_mpairs; p0 += kBatchPairs) {     // L2-sized batches of queries
         a.mp_base = p0;
         a.n_mpairs = std::min(kBatchPairs, n_mpairs - p0);
-        const int grid = (int)std::min<int64_t>((int64_t)a.n_mpairs * a.n_split, sms);
+        const int grid = (int)std::min<int64_t>(2 * (int64_t)a.n_mpairs * a.n_split, sms);
         KernelTimer timer("tree_scan", s);
         if (pre)
             bf_tc_kernel<MODE_TREE, true><<<grid, kernel_threads(true), smem_bytes(MODE_TREE), s>>>(a);

@@ -53,6 +53,19 @@ __device__ __forceinline__ uint64_t smem_desc_kmajor(uint32_t saddr, uint32_t lb
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// Shared-memory matrix descriptor, K-major operand with the 128-byte
+// swizzle: every row holds 128 bytes of K, 8 rows form a 1 KB atom (atoms
+// `sbo` bytes apart), and inside an atom the 16-byte unit j of row r is
+// stored at unit j ^ r.  The atoms must be 1 KB aligned; a K step inside
+// the atom starts at the atom base plus the step's byte offset, and the
+// leading-byte offset is unused (encoded 1).  Layout type 2 at bits 61-63
+// selects the 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr, uint32_t sbo)
+{
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (2ull << 61);
+}
+
 // Instruction descriptor for kind::f8f6f4 with E4M3 A and B (K-major), FP32
 // accumulation: D format bits [4,6) = 1, A/B formats [7,10)/[10,13) = 0,
 // N >> 3 at [17,23), M >> 4 at [24,29).
