@@ -297,17 +297,21 @@ struct TcArgs {
     const uint32_t *b_side;
 };
 
-// One work unit: query tile mt (< 0: absent, no tiles) against database
-// rows [r0, r1), taken in tiles of TN rows from r0 and multiplied NB tiles
-// per step; query rows >= nvalid are padding.  Unit u is query tile u % 2
-// of pair unit u / 2.
+// One work unit: query tile mt (< 0: absent) against database rows
+// [r0, r1), taken in tiles of TN rows from r0 and multiplied NB tiles per
+// step; query rows >= nvalid are padding.  Unit u is query tile u % 2 of
+// pair unit u / 2.  An absent tile has no tiles to multiply, except in
+// lock-step kernels (LOCK: both CTAs of a cluster walk the pair's steps
+// together), where it multiplies the pair's first tile (mt_a) and keeps
+// nothing.
 struct Unit {
-    int64_t mt;
+    int64_t mt, mt_a;
     int64_t r0, r1, ntiles, sp, out_base;
     int64_t mp, t0;                  // split mode: query-tile pair, first global tile
     int nvalid;
 };
 
+template <bool LOCK = false>
 __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
 {
     Unit v;
@@ -316,6 +320,7 @@ __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
     if (a.units) {
         const TcUnit t = a.units[pu];
         v.mt = qh ? t.a_tile1 : t.a_tile0;
+        v.mt_a = v.mt;
         v.nvalid = qh ? t.nvalid1 : t.nvalid0;
         v.r0 = t.row0;
         v.r1 = t.row1;
@@ -334,9 +339,10 @@ __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
         v.r1 = a.n;
         const int64_t mt = QT * mp + qh;
         v.mt = mt < a.n_mtiles ? mt : -1;
+        v.mt_a = v.mt >= 0 ? v.mt : (LOCK ? QT * mp : -1);
         v.nvalid = mt < a.n_mtiles ? (int)min((int64_t)TM, a.nq - mt * TM) : 0;
     }
-    if (v.mt < 0) v.ntiles = 0;
+    if (v.mt_a < 0) v.ntiles = 0;
     else if (a.units) v.ntiles = (v.r1 - v.r0 + TN - 1) / TN;
     else v.ntiles = min(a.n_ntiles, v.t0 + a.tiles_per_split) - v.t0;
     return v;
@@ -472,7 +478,8 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         for (int s = 0; s < STAGES; ++s) {
             // A (and with PRE, B) bytes + one arrival per producer warp
             mbar_init(&ctl->full[s], PRE ? 1 : 1 + PROD_WARPS);
-            mbar_init(&ctl->empty[s], 1);
+            // PRE: the MMAs of both CTAs of the cluster read the stage
+            mbar_init(&ctl->empty[s], PRE ? 2 : 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&ctl->acc_full[a], 1);
@@ -488,6 +495,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
     }
     tc_fence_before();
     __syncthreads();
+    if (PRE) cluster_sync_all();      // the partner's barriers exist before any copy
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
@@ -495,18 +503,21 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
 
     if (PRE && warp == EPI) {
         // ------------------------------------------------ copy issuer (PRE)
-        // The database arrives widened: one thread issues, per chunk, the
-        // query tile's chunk and the chunks of the step's database tiles,
-        // and with a step's last chunk the tiles' |t| records into the ring
-        // (at the same point of the sequence where the producers below
-        // write them).
+        // The database arrives widened.  The two CTAs of a cluster hold the
+        // two query tiles of a pair and walk the same steps: per chunk each
+        // brings its query tile's chunk, and CTA rank h brings the chunk of
+        // the step's database tile h into both CTAs (multicast), so every
+        // database chunk is read once per pair.  With a step's last chunk
+        // each CTA also copies the tiles' |t| records into its ring (at the
+        // same point of the sequence where the producers below write them).
         if (lane == 0) {
+            const uint32_t rank = cluster_rank();
             uint32_t g = 0, t = 0;
             // query tiles are read again for every database tile: kept in
             // L2; the widened database streams past once per CTA wave
             const uint64_t keep = l2_keep_policy(), stream = l2_stream_policy();
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
-                const Unit uv = get_unit(args, u);
+                const Unit uv = get_unit<PRE>(args, u);
                 for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
                      st = first_step<MODE>(args, uv, step_end(st)), ++t) {
                     const int64_t gt0 = uv.t0 + st.lt[0];
@@ -523,14 +534,13 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                         const uint32_t bytes = A_STAGE + nb * B_STAGE + (c == last_c ? nb * SIDE_BYTES : 0u);
                         mbar_arrive_expect_tx(&ctl->full[s], bytes);
                         unsigned char *dst = smem + (size_t)s * STAGE;
-                        bulk_g2s_hint(dst, args.a_exp + ((size_t)uv.mt * NCHUNK + c) * A_STAGE,
+                        bulk_g2s_hint(dst, args.a_exp + ((size_t)uv.mt_a * NCHUNK + c) * A_STAGE,
                                       (uint32_t)A_STAGE, &ctl->full[s], keep);
-                        bulk_g2s_hint(dst + A_STAGE, args.b_exp + ((size_t)gt0 * NCHUNK + c) * B_STAGE,
-                                      (uint32_t)B_STAGE, &ctl->full[s], stream);
-                        if (gt1 >= 0)
-                            bulk_g2s_hint(dst + A_STAGE + B_STAGE,
-                                          args.b_exp + ((size_t)gt1 * NCHUNK + c) * B_STAGE,
-                                          (uint32_t)B_STAGE, &ctl->full[s], stream);
+                        const int64_t gt = rank ? gt1 : gt0;
+                        if (gt >= 0)
+                            bulk_g2s_mc_hint(dst + A_STAGE + rank * B_STAGE,
+                                             args.b_exp + ((size_t)gt * NCHUNK + c) * B_STAGE,
+                                             (uint32_t)B_STAGE, &ctl->full[s], 0x3, stream);
                         if (c == last_c) {
                             bulk_g2s_hint(slot, args.b_side + (size_t)gt0 * SIDE_WORDS, SIDE_BYTES,
                                           &ctl->full[s], stream);
@@ -636,7 +646,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         if (lane == 0) {
             uint32_t g = 0, t = 0;
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
-                const Unit uv = get_unit(args, u);
+                const Unit uv = get_unit<PRE>(args, u);
                 for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
                      st = first_step<MODE>(args, uv, step_end(st)), ++t) {
                     const uint32_t acc = t & 1u, ra = t >> 1;
@@ -658,7 +668,10 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                                      smem_desc_sw128(b_base + kk * 32u, SBO), IDESC,
                                      (!first || kk != 0) ? 1u : 0u);
                         first = false;
-                        mma_commit(&ctl->empty[s]);
+                        // PRE: the stage holds chunks the partner brought in
+                        // and is refilled by both CTAs: free it in both
+                        if (PRE) mma_commit_mc(&ctl->empty[s], 0x3);
+                        else mma_commit(&ctl->empty[s]);
                     }
                     mma_commit(&ctl->acc_full[acc]);
                 }
@@ -682,7 +695,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         uint64_t L[kMaxK];
         uint32_t t = 0;
         for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x) {
-            const Unit uv = get_unit(args, u);
+            const Unit uv = get_unit<PRE>(args, u);
             const int64_t qi = uv.mt * TM + row;      // query (split mode) or pair slot (list mode)
             const bool valid = uv.mt >= 0 && row < uv.nvalid;
             const QueryWeights w = query_weights(valid ? args.qpop[qi] : 0u);
@@ -791,6 +804,9 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
 done:
     tc_fence_before();
     __syncthreads();
+    // PRE: no CTA leaves while its partner may still copy into it or
+    // release its stages
+    if (PRE) cluster_sync_all();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
@@ -819,6 +835,66 @@ __global__ void merge_top1_kernel(const uint64_t *__restrict__ partial, int n_sp
 // database tile when a call has more queries than L2 holds.
 constexpr int kBatchPairs = 48;
 
+// Pre-widened kernels run as clusters of two CTAs (the two query tiles of
+// a pair).  Launch configuration, and how many such clusters the device
+// holds at once (queried once per device and kernel mode; 0 when none
+// fits, and then the in-kernel widening is used).
+template <int MODE>
+cudaLaunchConfig_t pre_config(int grid, cudaStream_t s, cudaLaunchAttribute *attr)
+{
+    cudaLaunchConfig_t c{};
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    c.gridDim = dim3((unsigned)grid);
+    c.blockDim = dim3((unsigned)kernel_threads(true));
+    c.dynamicSmemBytes = smem_bytes(MODE);
+    c.stream = s;
+    c.attrs = attr;
+    c.numAttrs = 1;
+    return c;
+}
+
+template <int MODE>
+int pre_clusters()
+{
+    static std::mutex mu;
+    static int cached[64];
+    static bool known[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 0;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!known[dev]) {
+        int n = 0;
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t c = pre_config<MODE>(2, nullptr, attr);
+        if (allow_smem((const void *)bf_tc_kernel<MODE, true>, (int)smem_bytes(MODE)) != cudaSuccess ||
+            cudaOccupancyMaxActiveClusters(&n, (const void *)bf_tc_kernel<MODE, true>, &c) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        cached[dev] = n;
+        known[dev] = true;
+    }
+    return cached[dev];
+}
+
+// Launch a pre-widened kernel over `units` units (an even number: pairs).
+template <int MODE>
+cudaError_t launch_pre(const TcArgs &a, int64_t units, cudaStream_t s)
+{
+    const int ncl = pre_clusters<MODE>();
+    if (ncl < 1) return cudaErrorLaunchOutOfResources;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t c =
+        pre_config<MODE>((int)(2 * std::min<int64_t>(ncl, (units + 1) / 2)), s, attr);
+    return cudaLaunchKernelEx(&c, bf_tc_kernel<MODE, true>, a);
+}
+
 // Should a split-mode scan of n rows by nq queries read a pre-widened copy
 // of the rows (kernel variant PRE)?  The copy costs one pass writing
 // n * 4 KB (8x the rows) and that much scratch; it spares every unit the
@@ -827,6 +903,7 @@ constexpr int kBatchPairs = 48;
 bool want_prewiden(int64_t n, int64_t nq, int forced)
 {
     if (forced == 1) return false;
+    if (pre_clusters<MODE_PLAIN>() < 1 || pre_clusters<MODE_TREE>() < 1) return false;
     if (forced == 2) return true;
     if (nq < 8 * TM) return false;
     size_t free_b = 0, total_b = 0;
@@ -934,7 +1011,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
         const int grid = (int)std::min<int64_t>(2 * (int64_t)a.n_mpairs * n_split, sms);
         KernelTimer timer("tc_scan", s);
         if (pre)
-            bf_tc_kernel<MODE_PLAIN, true><<<grid, kernel_threads(true), smem_bytes(MODE_PLAIN), s>>>(a);
+            DT_CUDA_TRY(launch_pre<MODE_PLAIN>(a, 2 * (int64_t)a.n_mpairs * n_split, s));
         else
             bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
         DT_CUDA_TRY(cudaGetLastError());
@@ -1128,7 +1205,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
         const int grid = (int)std::min<int64_t>(2 * (int64_t)a.n_mpairs * a.n_split, sms);
         KernelTimer timer("tree_scan", s);
         if (pre)
-            bf_tc_kernel<MODE_TREE, true><<<grid, kernel_threads(true), smem_bytes(MODE_TREE), s>>>(a);
+            DT_CUDA_TRY(launch_pre<MODE_TREE>(a, 2 * (int64_t)a.n_mpairs * a.n_split, s));
         else
             bf_tc_kernel<MODE_TREE, false><<<grid, kernel_threads(false), smem_bytes(MODE_TREE), s>>>(a);
         DT_CUDA_TRY(cudaGetLastError());

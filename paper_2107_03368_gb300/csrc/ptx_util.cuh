@@ -108,4 +108,33 @@ __device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32
         : "memory");
 }
 
+// bulk_g2s_hint delivered to every CTA of the cluster named in `mask`
+// (bit i: CTA rank i), at the same shared-memory offset in each, and
+// completing `bytes` on the mbarrier at the offset of `bar` in each.
+__device__ __forceinline__ void bulk_g2s_mc_hint(void *dst, const void *src, uint32_t bytes,
+                                                 uint64_t *bar, uint16_t mask, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        ".L2::cache_hint [%0], [%1], %2, [%3], %4, %5;"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask), "l"(policy)
+        : "memory");
+}
+
+// Rank of this CTA in its cluster.
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster: writes before the barrier
+// (shared-memory barrier initialisation included) are visible to the
+// cluster after it.
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 }  // namespace dtk

@@ -95,6 +95,16 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
         ::"r"(smem_u32(bar)) : "memory");
 }
 
+// mma_commit to the mbarrier at the offset of `bar` in every CTA of the
+// cluster named in `mask` (bit i: CTA rank i).
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;"
+        ::"r"(smem_u32(bar)), "h"(mask) : "memory");
+}
+
 // --- TMEM -> registers: 32 lanes x 32 consecutive 32-bit columns ------------
 __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)[32])
 {
