@@ -244,6 +244,23 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity, Tc
     return false;
 }
 
+// As wait_or_abort for the two single threads that feed the tensor cores
+// (copy issuer, MMA issuer): they poll without sleeping, so a stage is
+// refilled or multiplied as soon as its barrier completes.  Bounded by
+// elapsed SM clocks (about two seconds).
+__device__ __forceinline__ bool wait_spin(uint64_t *bar, uint32_t parity, TcCtl *ctl, uint32_t *err)
+{
+    const long long t0 = clock64();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (ctl->abort) return false;
+        if ((i & 255u) == 255u && clock64() - t0 > (4ll << 30)) break;
+    }
+    ctl->abort = 1u;
+    atomicOr(err, 1u);
+    return false;
+}
+
 // Warp-uniform version: lane 0 waits, the verdict is broadcast.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, TcCtl *ctl, uint32_t *err,
                                           int lane)
@@ -290,6 +307,10 @@ struct TcArgs {
     const uint32_t *kmask;
     const uint32_t *cap;
     uint32_t *need_out;
+    // Split mode: per query, the smallest k-th key of any full list so far
+    // (a key >= the exact k-th result's key, as `cap`), shared by all the
+    // query's lists while they are built; 0xFFFFFFFF at the start.
+    uint32_t *gcap;
     // Pre-widened database (split mode, PRE kernels): stage images
     // b_exp[tile][chunk][B_STAGE] of global tile `tile` (rows 128 tile ..),
     // and per tile its |t| record b_side[tile][SIDE_WORDS].
@@ -530,7 +551,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                         const int c = __ffs(m) - 1;
                         const int s = (int)(g % STAGES);
                         const uint32_t r = g / STAGES;
-                        if (!wait_or_abort(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err)) goto done;
+                        if (!wait_spin(&ctl->empty[s], (r & 1u) ^ 1u, ctl, err)) goto done;
                         const uint32_t bytes = A_STAGE + nb * B_STAGE + (c == last_c ? nb * SIDE_BYTES : 0u);
                         mbar_arrive_expect_tx(&ctl->full[s], bytes);
                         unsigned char *dst = smem + (size_t)s * STAGE;
@@ -650,7 +671,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                 for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
                      st = first_step<MODE>(args, uv, step_end(st)), ++t) {
                     const uint32_t acc = t & 1u, ra = t >> 1;
-                    if (!wait_or_abort(&ctl->acc_empty[acc], (ra & 1u) ^ 1u, ctl, err)) goto mma_done;
+                    if (!wait_spin(&ctl->acc_empty[acc], (ra & 1u) ^ 1u, ctl, err)) goto mma_done;
                     tc_fence_after();
                     const uint32_t d_tmem = tmem + acc * ACC_COLS;
                     uint32_t km = step_mask<MODE>(args, uv, st);
@@ -658,7 +679,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                     for (; km; km &= km - 1, ++g) {
                         const int s = (int)(g % STAGES);
                         const uint32_t r = g / STAGES;
-                        if (!wait_or_abort(&ctl->full[s], r & 1u, ctl, err)) goto mma_done;
+                        if (!wait_spin(&ctl->full[s], r & 1u, ctl, err)) goto mma_done;
                         tc_fence_after();
                         const uint32_t a_base = smem_u32(smem + (size_t)s * STAGE);
                         const uint32_t b_base = a_base + A_STAGE;
@@ -702,7 +723,8 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
             // a cap known to be >= the exact k-th key: nothing above it is kept
             const uint32_t capk =
                 (MODE != MODE_PLAIN && args.cap && valid) ? __ldg(args.cap + qi) : 0xFFFFFFFFu;
-            const uint64_t capw = capk == 0xFFFFFFFFu ? kEmpty : pack(capk, 0xFFFFFFFFu);
+            uint64_t capw = capk == 0xFFFFFFFFu ? kEmpty : pack(capk, 0xFFFFFFFFu);
+            uint32_t published = capk;        // the largest key not worth publishing
             // key = A*Z + B*P = (|q| - O) Z + (|t| - O) P = |t| P + |q| Z - O (Z + P).
             // The bit pattern F of 4096 * sum + 2^23 is 0x4B000000 + O, so
             // key = |t| P + (|q| Z + 0x4B000000 (Z + P)) - F (Z + P) in
@@ -715,6 +737,17 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
             for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
                  st = first_step<MODE>(args, uv, step_end(st)), ++t) {
                 const uint32_t acc = t & 1u, ra = t >> 1;
+                if (MODE != MODE_BOUND && args.gcap && valid) {
+                    // the query's other lists may have found closer rows:
+                    // nothing above their k-th key can be in the result
+                    const uint32_t gc = __ldcg(args.gcap + qi);
+                    if (gc < wkey) {
+                        capw = pack(gc, 0xFFFFFFFFu);
+                        worst = worst < capw ? worst : capw;
+                        wkey = (uint32_t)(worst >> 32);
+                        published = gc;
+                    }
+                }
                 if (!warp_wait(&ctl->acc_full[acc], ra & 1u, ctl, err, lane)) goto done;
                 tc_fence_after();
                 const uint32_t *side = ring + (t % TP_RING) * (NB * SIDE_WORDS);
@@ -784,7 +817,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                         for (int j = 0; j < 32; ++j) {
                             if ((bits >> j) & 1u) {
                                 worst = list_insert(L, k, v[j], b0 + j, args.idx_map, worst);
-                                if (MODE == MODE_TREE) worst = worst < capw ? worst : capw;
+                                worst = worst < capw ? worst : capw;
                                 wkey = (uint32_t)(worst >> 32);
                             }
                         }
@@ -793,6 +826,12 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&ctl->acc_empty[acc]);
+                if (MODE != MODE_BOUND && args.gcap && valid && wkey < published &&
+                    L[k - 1] != kEmpty) {
+                    // a full list: its k-th key bounds the query's result
+                    atomicMin(args.gcap + qi, wkey);
+                    published = wkey;
+                }
             }
             if (MODE != MODE_BOUND && valid) {
                 uint64_t *out = args.units ? args.partial + (uv.out_base + qi) * k
@@ -977,6 +1016,9 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_lists * nq * k * 8));
     // lists start empty: a block that gives up on a wait leaves valid lists
     DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_lists * nq * k * 8, s));
+    uint32_t *gcap = nullptr;
+    DT_CUDA_TRY(scratch.alloc(&gcap, (size_t)nq * 4));
+    DT_CUDA_TRY(cudaMemsetAsync(gcap, 0xFF, (size_t)nq * 4, s));
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
     const int64_t items = (int64_t)n_mtiles * TM * NCHUNK;
     widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(q, nq, n_mtiles, a_exp, qpop);
@@ -998,6 +1040,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.n_units = nullptr;
     a.partial = partial;
     a.err = err;
+    a.gcap = gcap;
     if (pre) {
         unsigned char *b_exp = nullptr;
         uint32_t *b_side = nullptr;
@@ -1192,6 +1235,10 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_lists * nq * k * 8));
     DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_lists * nq * k * 8, s));
     a.partial = partial;
+    uint32_t *gcap = nullptr;
+    DT_CUDA_TRY(scratch.alloc(&gcap, (size_t)n_mtiles * TM * 4));
+    DT_CUDA_TRY(cudaMemsetAsync(gcap, 0xFF, (size_t)n_mtiles * TM * 4, s));
+    a.gcap = gcap;
     if (pre) {
         unsigned char *b_exp = nullptr;
         uint32_t *b_side = nullptr;
