@@ -148,9 +148,30 @@ int dt_build(const uint64_t *d_db, int64_t n, const dt_build_params *params, voi
  * no-op.
  * Errors: DT_EINVAL (null index, m < 0, n + m > DT_MAX_N - 65536, null or
  * misaligned d_new with m > 0, another current device), DT_ENOMEM, DT_ECUDA.
- * On every error the index is left as it was.
+ * On every error the index is left as it was.  An index that keeps a
+ * widened copy (dt_keep_widened) has it rebuilt after the rows move; when
+ * the new copy does not fit it is dropped and the call still succeeds
+ * (searches stay exact, only slower).
  */
 int dt_insert(dt_index *index, const uint64_t *d_new, int64_t m, void *stream);
+
+/*
+ * dt_keep_widened — keep (on = 1) or release (on = 0) a resident copy of the
+ * index's tree-ordered descriptors widened for the tensor cores.  Not a
+ * step of the paper's method: the batched traversal of dt_search (§4.2 with
+ * the sequential scan of §6.2 on the tensor cores) multiplies the rows as
+ * FP8 E4M3 bytes (one byte per bit), and without a kept copy every call
+ * widens the whole database again (about 1.5 ms per million descriptors).
+ * Cost: 4,096 bytes per descriptor plus 528 bytes per 128 descriptors of
+ * device memory (41 GB at 10M), plain device allocations owned by the
+ * index until dt_free, dt_keep_widened(index, 0, ...) or an insertion that
+ * no longer leaves room.  Results never change.  The widening runs on
+ * `stream` and is complete on return; call it while no search of the index
+ * is running.  The current device must be the index's.
+ * Errors: DT_EINVAL (null index, on not 0 or 1, another current device),
+ * DT_ENOMEM (the copy does not fit; the index is unchanged), DT_ECUDA.
+ */
+int dt_keep_widened(dt_index *index, int32_t on, void *stream);
 
 /*
  * QUICCI descriptors (§2.2) of oriented points on a triangle mesh, or the

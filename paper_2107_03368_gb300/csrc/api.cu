@@ -212,7 +212,29 @@ int dt_insert(dt_index *ix, const uint64_t *d_new, int64_t m, void *stream)
     int dev = -1;
     DT_CUDA_TRY(cudaGetDevice(&dev));
     DT_CHECK_ARG(dev == ix->device, "the current device must be the index's device");
-    return insert_tree(ix, d_new, m, (cudaStream_t)stream);
+    const bool kept = ix->scan_exp != nullptr;
+    const int rc = insert_tree(ix, d_new, m, (cudaStream_t)stream);
+    if (rc == DT_OK && kept) {
+        // the rows moved: rebuild the kept widened copy, or leave it off
+        // when it no longer fits (searches stay exact, only slower)
+        if (int r = index_keep_widened(ix, false, (cudaStream_t)stream)) return r;
+        const int r = index_keep_widened(ix, true, (cudaStream_t)stream);
+        if (r != DT_OK && r != DT_ENOMEM) return r;
+    }
+    return rc;
+}
+
+int dt_keep_widened(dt_index *ix, int32_t on, void *stream)
+{
+    g_last_error.clear();
+    DT_CHECK_ARG(ix != nullptr, "index must not be NULL");
+    DT_CHECK_ARG(on == 0 || on == 1, "on must be 0 or 1");
+    int dev = -1;
+    DT_CUDA_TRY(cudaGetDevice(&dev));
+    DT_CHECK_ARG(dev == ix->device, "the current device must be the index's device");
+    const int rc = index_keep_widened(ix, on != 0, (cudaStream_t)stream);
+    if (rc == DT_ENOMEM) set_error("no room for the widened copy (4 KB per descriptor)");
+    return rc;
 }
 
 int quicci_generate(const float *d_vertices, int64_t n_vertices, const int32_t *d_triangles,
@@ -464,6 +486,8 @@ void dt_free(dt_index *ix)
     cudaFree(ix->node);
     cudaFree(ix->tile_or);
     cudaFree(ix->tile_kmask);
+    cudaFree(ix->scan_exp);
+    cudaFree(ix->scan_side);
     cudaSetDevice(cur);
     delete ix;
 }

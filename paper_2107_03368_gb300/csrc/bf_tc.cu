@@ -964,24 +964,32 @@ int64_t step_tiles(int64_t n_tiles, int splits)
 
 // Stage images and |t| records of rows [0, n) of db, tiled by TN rows
 // (rows past n are zero), from `scratch`.
-int prewiden_rows(const uint64_t *db, int64_t n, Scratch &scratch, cudaStream_t s,
-                  unsigned char **b_exp, uint32_t **b_side)
+// Widen rows [0, n) into b_exp / b_side (sized as in prewiden_rows).
+int widen_rows_into(const uint64_t *db, int64_t n, unsigned char *b_exp, uint32_t *b_side,
+                    Scratch &scratch, cudaStream_t s)
 {
     const int64_t n_tiles = (n + TN - 1) / TN;
     uint32_t *rowpop = nullptr;
-    DT_CUDA_TRY(scratch.alloc(b_exp, (size_t)n_tiles * NCHUNK * B_STAGE));
-    DT_CUDA_TRY(scratch.alloc(b_side, (size_t)n_tiles * SIDE_BYTES));
     DT_CUDA_TRY(scratch.alloc(&rowpop, (size_t)n_tiles * TN * 4));
     static_assert(TN == TM && B_STAGE == A_STAGE, "database tiles widen like query tiles");
     const int64_t items = n_tiles * TN * NCHUNK;
     {
         KernelTimer timer("prewiden", s);
-        widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(db, n, (int)n_tiles, *b_exp,
+        widen_queries_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(db, n, (int)n_tiles, b_exp,
                                                                              rowpop);
-        side_kernel<<<(unsigned)n_tiles, TN, 0, s>>>(rowpop, n, *b_side);
+        side_kernel<<<(unsigned)n_tiles, TN, 0, s>>>(rowpop, n, b_side);
     }
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
+}
+
+int prewiden_rows(const uint64_t *db, int64_t n, Scratch &scratch, cudaStream_t s,
+                  unsigned char **b_exp, uint32_t **b_side)
+{
+    const int64_t n_tiles = (n + TN - 1) / TN;
+    DT_CUDA_TRY(scratch.alloc(b_exp, (size_t)n_tiles * NCHUNK * B_STAGE));
+    DT_CUDA_TRY(scratch.alloc(b_side, (size_t)n_tiles * SIDE_BYTES));
+    return widen_rows_into(db, n, *b_exp, *b_side, scratch, s);
 }
 
 // Per-split top-k lists of every query over db (rows reported through
@@ -1230,7 +1238,10 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     a.kmask = ix->tile_kmask;
     a.cap = cap_slot;
     a.err = err;
-    const bool pre = want_prewiden(n, nq, c.b);
+    // a resident widened copy costs nothing per call: use it unless forced off
+    const bool pre = ix->scan_exp && c.b != 1 && pre_clusters<MODE_TREE>() > 0
+                         ? true
+                         : want_prewiden(n, nq, c.b);
     const int n_lists = a.n_split * lists_per_unit(pre);
     DT_CUDA_TRY(scratch.alloc(&partial, (size_t)n_lists * nq * k * 8));
     DT_CUDA_TRY(cudaMemsetAsync(partial, 0xFF, (size_t)n_lists * nq * k * 8, s));
@@ -1239,7 +1250,10 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     DT_CUDA_TRY(scratch.alloc(&gcap, (size_t)n_mtiles * TM * 4));
     DT_CUDA_TRY(cudaMemsetAsync(gcap, 0xFF, (size_t)n_mtiles * TM * 4, s));
     a.gcap = gcap;
-    if (pre) {
+    if (pre && ix->scan_exp) {
+        a.b_exp = ix->scan_exp;
+        a.b_side = ix->scan_side;
+    } else if (pre) {
         unsigned char *b_exp = nullptr;
         uint32_t *b_side = nullptr;
         if (int r = prewiden_rows(ix->db_tree, n, scratch, s, &b_exp, &b_side)) return r;
@@ -1266,6 +1280,51 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     *partial_out = partial;
     *n_split_out = n_lists;
     *need_words_out = need_words;
+    return DT_OK;
+}
+
+// Keep (on) or release (off) the index's resident widened copy of its
+// tree-ordered rows.  The arrays are plain device allocations owned by the
+// index; the widening runs on stream s and is complete on return.
+int index_keep_widened(dt_index *ix, bool on, cudaStream_t s)
+{
+    if (!on) {
+        if (ix->scan_exp || ix->scan_side) {
+            DT_CUDA_TRY(cudaStreamSynchronize(s));
+            cudaFree(ix->scan_exp);
+            cudaFree(ix->scan_side);
+            ix->scan_exp = nullptr;
+            ix->scan_side = nullptr;
+        }
+        return DT_OK;
+    }
+    if (ix->scan_exp) return DT_OK;
+    const int64_t n_tiles = (ix->n + TN - 1) / TN;
+    const size_t exp_bytes = (size_t)n_tiles * NCHUNK * B_STAGE, side_bytes = (size_t)n_tiles * SIDE_BYTES;
+    unsigned char *e = nullptr;
+    uint32_t *sd = nullptr;
+    if (cudaMalloc(&e, exp_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return DT_ENOMEM;
+    }
+    if (cudaMalloc(&sd, side_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(e);
+        return DT_ENOMEM;
+    }
+    int rc = DT_OK;
+    {
+        Scratch scratch(s);
+        rc = widen_rows_into(ix->db_tree, ix->n, e, sd, scratch, s);
+    }
+    if (rc == DT_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = DT_ECUDA;
+    if (rc != DT_OK) {
+        cudaFree(e);
+        cudaFree(sd);
+        return rc;
+    }
+    ix->scan_exp = e;
+    ix->scan_side = sd;
     return DT_OK;
 }
 

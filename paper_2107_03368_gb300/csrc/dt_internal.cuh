@@ -269,6 +269,11 @@ struct dt_index {
     // chunk c (words 2c, 2c + 1).  ceil(n / 128) entries each.
     uint64_t *tile_or = nullptr;
     uint32_t *tile_kmask = nullptr;
+    // Optional (dt_keep_widened): the tree-ordered rows as FP8 stage images
+    // of the tensor-core scan, [scan tile][128-bit chunk][16 KB], and each
+    // scan tile's |t| record; null when not kept.
+    unsigned char *scan_exp = nullptr;
+    uint32_t *scan_side = nullptr;
 };
 
 namespace dtk {
@@ -342,6 +347,8 @@ int launch_dt_search_batched(const dt_index *ix, const uint64_t *q, int64_t nq, 
 // tiles, skipping K chunks the tile has no bit in, into per-split sorted
 // lists partial[split][slot][k] of (key, original index).  *need (host
 // copy, n_mpairs x need_words words) is filled when need_host is non-null.
+// dt_keep_widened: build (on) or release (off) ix->scan_exp / scan_side.
+int index_keep_widened(dt_index *ix, bool on, cudaStream_t s);
 int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int32_t *slot_q,
                    const uint32_t *cap_slot, int n_mtiles, int k, Scratch &scratch, cudaStream_t s,
                    uint64_t **partial_out, int *n_split_out, std::vector<uint32_t> *need_host,

@@ -79,6 +79,7 @@ def load():
         sig = {
             "dt_build": ([P, i64, P, P, P], ctypes.c_int),
             "dt_insert": ([P, P, i64, P], ctypes.c_int),
+            "dt_keep_widened": ([P, i32, P], ctypes.c_int),
             "dt_save": ([P, ctypes.c_char_p], ctypes.c_int),
             "dt_load": ([ctypes.c_char_p, P, i64, P, P], ctypes.c_int),
             "quicci_generate": ([P, i64, P, i64, P, P, i64, ctypes.c_float, i32, P, P],
@@ -211,6 +212,13 @@ def dt_insert(index: Index, new, stream=None) -> Index:
     they take original indices n .. n+m-1.  Returns ``index``."""
     new = _desc(new, "new")
     _check(load().dt_insert(index.handle, _ptr(new), new.shape[0], _stream(stream)), "dt_insert")
+    return index
+
+
+def dt_keep_widened(index: Index, on: bool = True, stream=None) -> Index:
+    """Keeps (or releases) the index's resident tensor-core copy of its rows
+    (4 KB per descriptor), so batched searches skip widening them per call."""
+    _check(load().dt_keep_widened(index.handle, 1 if on else 0, _stream(stream)), "dt_keep_widened")
     return index
 
 

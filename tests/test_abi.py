@@ -57,6 +57,7 @@ def test_bad_sizes_are_rejected():
     assert lib.retrieve_objects(None, None, 3, None, None, 1, 10, 0, 0, None, None, None, 0,
                                 None) == dt.DT_EINVAL
     assert lib.dt_get_info(None, None) == dt.DT_EINVAL
+    assert lib.dt_keep_widened(None, 1, None) == dt.DT_EINVAL
 
 
 def test_new_entry_points_check_their_arguments_first():

@@ -247,3 +247,38 @@ def test_search_after_insert_and_reload(tmp_path, path):
     idx, score, ab, _ = dt.dt_search_path(back, to_dev(q), 6, path, with_ab=True)
     assert_matches_oracle(db, q, 6, idx, score, ab)
 
+
+
+@pytest.mark.parametrize("n,nq,k", [(50_077, 1_037, 10), (9_000, 300, 32)])
+def test_kept_widened_copy_changes_nothing(n, nq, k):
+    """dt_keep_widened keeps the tree-ordered rows widened in the index; the
+    batched traversal then reads that copy instead of widening per call:
+    the same indices, scores and (A, B) as without it, and the oracle's
+    top-k; released again, the search still matches."""
+    db = mixed_db(n + 3, n, per_object=500)
+    q = edge_queries(nq + 3, db, nq - 5)
+    d_q = to_dev(q)
+    ix = dt.dt_build(to_dev(db))
+    ref = dt.dt_search_path(ix, d_q, k, 2, with_ab=True)
+    dt.dt_keep_widened(ix, True)
+    got = dt.dt_search_path(ix, d_q, k, 2, with_ab=True)
+    for a, b in zip(got[:3], ref[:3]):
+        assert torch_equal(a, b)
+    pick = np.unique(np.linspace(0, q.shape[0] - 1, 100).astype(np.int64))
+    assert_matches_oracle(db, q[pick], k, got[0][pick], got[1][pick], got[2][pick])
+    dt.dt_keep_widened(ix, False)
+    again = dt.dt_search_path(ix, d_q, k, 2, with_ab=True)
+    for a, b in zip(again[:3], ref[:3]):
+        assert torch_equal(a, b)
+
+
+def test_kept_widened_copy_follows_insertion():
+    """An insertion moves the rows; the kept copy is rebuilt with them."""
+    db = mixed_db(95, 14_000, per_object=400)
+    q = edge_queries(96, db, 1_100)
+    ix = dt.dt_build(to_dev(db[:10_000]))
+    dt.dt_keep_widened(ix, True)
+    dt.dt_insert(ix, to_dev(db[10_000:]))
+    idx, score, ab, _ = dt.dt_search_path(ix, to_dev(q), 7, 2, with_ab=True)
+    pick = np.unique(np.linspace(0, q.shape[0] - 1, 120).astype(np.int64))
+    assert_matches_oracle(db, q[pick], 7, idx[pick], score[pick], ab[pick])
