@@ -373,7 +373,7 @@ __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
         v.r1 = t.row1;
         v.sp = 0;
         v.mp = 0;
-        v.t0 = 0;
+        v.t0 = t.tile0;
         v.out_base = t.out_base;
     } else {
         const int64_t mp = a.mp_base + pu % a.n_mpairs;
@@ -501,7 +501,10 @@ __device__ __noinline__ uint64_t list_insert(uint64_t *L, int k, uint32_t key, i
     return L[k - 1];
 }
 
-template <int MODE, bool PRE>
+// PRE: database chunks arrive pre-widened by bulk copies; CL (split mode,
+// implies PRE): the two CTAs of a cluster hold a pair's two query tiles and
+// multicast the database chunks to each other.
+template <int MODE, bool PRE, bool CL>
 __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcArgs args)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -517,16 +520,18 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
     uint32_t *err = args.err;
 
     constexpr int EPI = epi_warps(PRE), MMAW = mma_warp(PRE);
-    // slice groups: one per 4 epilogue warps in split mode, a single one
-    // (one list per slot) in list mode
-    const int ngroups = args.units ? 1 : EPI / 4;
+    static_assert(PRE || !CL, "clusters share pre-widened chunks");
+    // slice groups: one per 4 epilogue warps, each with its own list per
+    // query; in list mode (one list per slot) a single group, except for
+    // k = 1, where the groups merge into the slot's entry by atomic minimum
+    const int ngroups = args.units && args.k > 1 ? 1 : EPI / 4;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             // A (and with PRE, B) bytes + one arrival per producer warp
             mbar_init(&ctl->full[s], PRE ? 1 : 1 + PROD_WARPS);
-            // PRE: the MMAs of both CTAs of the cluster read the stage
-            mbar_init(&ctl->empty[s], PRE ? 2 : 1);
+            // CL: the MMAs of both CTAs of the cluster read the stage
+            mbar_init(&ctl->empty[s], CL ? 2 : 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&ctl->acc_full[a], 1);
@@ -542,7 +547,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
     }
     tc_fence_before();
     __syncthreads();
-    if (PRE) cluster_sync_all();      // the partner's barriers exist before any copy
+    if (CL) cluster_sync_all();       // the partner's barriers exist before any copy
     tc_fence_after();
     const uint32_t tmem = ctl->tmem_base;
 
@@ -558,13 +563,13 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         // each CTA also copies the tiles' |t| records into its ring (at the
         // same point of the sequence where the producers below write them).
         if (lane == 0) {
-            const uint32_t rank = cluster_rank();
+            const uint32_t rank = CL ? cluster_rank() : 0u;
             uint32_t g = 0, t = 0;
             // query tiles are read again for every database tile: kept in
             // L2; the widened database streams past once per CTA wave
             const uint64_t keep = l2_keep_policy(), stream = l2_stream_policy();
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
-                const Unit uv = get_unit<PRE>(args, u);
+                const Unit uv = get_unit<CL>(args, u);
                 for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
                      st = first_step<MODE>(args, uv, step_end(st)), ++t) {
                     const int64_t gt0 = uv.t0 + st.lt[0];
@@ -583,11 +588,20 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                         unsigned char *dst = smem + (size_t)s * STAGE;
                         bulk_g2s_hint(dst, args.a_exp + ((size_t)uv.mt_a * NCHUNK + c) * A_STAGE,
                                       (uint32_t)A_STAGE, &ctl->full[s], keep);
-                        const int64_t gt = rank ? gt1 : gt0;
-                        if (gt >= 0)
-                            bulk_g2s_mc_hint(dst + A_STAGE + rank * B_STAGE,
-                                             args.b_exp + ((size_t)gt * NCHUNK + c) * B_STAGE,
-                                             (uint32_t)B_STAGE, &ctl->full[s], 0x3, stream);
+                        if (CL) {
+                            const int64_t gt = rank ? gt1 : gt0;
+                            if (gt >= 0)
+                                bulk_g2s_mc_hint(dst + A_STAGE + rank * B_STAGE,
+                                                 args.b_exp + ((size_t)gt * NCHUNK + c) * B_STAGE,
+                                                 (uint32_t)B_STAGE, &ctl->full[s], 0x3, stream);
+                        } else {
+                            bulk_g2s_hint(dst + A_STAGE, args.b_exp + ((size_t)gt0 * NCHUNK + c) * B_STAGE,
+                                          (uint32_t)B_STAGE, &ctl->full[s], stream);
+                            if (gt1 >= 0)
+                                bulk_g2s_hint(dst + A_STAGE + B_STAGE,
+                                              args.b_exp + ((size_t)gt1 * NCHUNK + c) * B_STAGE,
+                                              (uint32_t)B_STAGE, &ctl->full[s], stream);
+                        }
                         if (c == last_c) {
                             bulk_g2s_hint(slot, args.b_side + (size_t)gt0 * SIDE_WORDS, SIDE_BYTES,
                                           &ctl->full[s], stream);
@@ -697,7 +711,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         if (lane == 0) {
             uint32_t g = 0, t = 0;
             for (int64_t u = blockIdx.x; u < total_units && !ctl->abort; u += gridDim.x) {
-                const Unit uv = get_unit<PRE>(args, u);
+                const Unit uv = get_unit<CL>(args, u);
                 for (Step st = first_step<MODE>(args, uv, 0); st.lt[0] < uv.ntiles;
                      st = first_step<MODE>(args, uv, step_end(st)), ++t) {
                     const uint32_t acc = t & 1u, ra = t >> 1;
@@ -719,9 +733,9 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                                      smem_desc_sw128(b_base + kk * 32u, SBO), IDESC,
                                      (!first || kk != 0) ? 1u : 0u);
                         first = false;
-                        // PRE: the stage holds chunks the partner brought in
+                        // CL: the stage holds chunks the partner brought in
                         // and is refilled by both CTAs: free it in both
-                        if (PRE) mma_commit_mc(&ctl->empty[s], 0x3);
+                        if (CL) mma_commit_mc(&ctl->empty[s], 0x3);
                         else mma_commit(&ctl->empty[s]);
                     }
                     mma_commit(&ctl->acc_full[acc]);
@@ -746,7 +760,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
         uint64_t L[kMaxK];
         uint32_t t = 0;
         for (int64_t u = blockIdx.x; u < total_units; u += gridDim.x) {
-            const Unit uv = get_unit<PRE>(args, u);
+            const Unit uv = get_unit<CL>(args, u);
             const int64_t qi = uv.mt * TM + row;      // query (split mode) or pair slot (list mode)
             const bool valid = uv.mt >= 0 && row < uv.nvalid;
             const QueryWeights w = query_weights(valid ? args.qpop[qi] : 0u);
@@ -866,16 +880,19 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
             if (MODE != MODE_BOUND && valid) {
                 uint64_t *out = args.units ? args.partial + (uv.out_base + qi) * k
                                            : args.partial + ((uv.sp * ngroups + grp) * nq + qi) * k;
-                for (int j = 0; j < k; ++j) out[j] = L[j];
+                if (args.units && ngroups > 1)      // k == 1: the groups share the entry
+                    atomicMin(reinterpret_cast<unsigned long long *>(out), (unsigned long long)L[0]);
+                else
+                    for (int j = 0; j < k; ++j) out[j] = L[j];
             }
         }
     }
 done:
     tc_fence_before();
     __syncthreads();
-    // PRE: no CTA leaves while its partner may still copy into it or
+    // CL: no CTA leaves while its partner may still copy into it or
     // release its stages
-    if (PRE) cluster_sync_all();
+    if (CL) cluster_sync_all();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, TMEM_COLS);
@@ -941,8 +958,8 @@ int pre_clusters()
         int n = 0;
         cudaLaunchAttribute attr[1];
         const cudaLaunchConfig_t c = pre_config<MODE>(2, nullptr, attr);
-        if (allow_smem((const void *)bf_tc_kernel<MODE, true>, (int)smem_bytes(MODE)) != cudaSuccess ||
-            cudaOccupancyMaxActiveClusters(&n, (const void *)bf_tc_kernel<MODE, true>, &c) != cudaSuccess) {
+        if (allow_smem((const void *)bf_tc_kernel<MODE, true, true>, (int)smem_bytes(MODE)) != cudaSuccess ||
+            cudaOccupancyMaxActiveClusters(&n, (const void *)bf_tc_kernel<MODE, true, true>, &c) != cudaSuccess) {
             cudaGetLastError();
             n = 0;
         }
@@ -961,7 +978,7 @@ cudaError_t launch_pre(const TcArgs &a, int64_t units, cudaStream_t s)
     cudaLaunchAttribute attr[1];
     const cudaLaunchConfig_t c =
         pre_config<MODE>((int)(2 * std::min<int64_t>(ncl, (units + 1) / 2)), s, attr);
-    return cudaLaunchKernelEx(&c, bf_tc_kernel<MODE, true>, a);
+    return cudaLaunchKernelEx(&c, bf_tc_kernel<MODE, true, true>, a);
 }
 
 // Should a split-mode scan of n rows by nq queries read a pre-widened copy
@@ -1028,8 +1045,8 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
                     int64_t nq, int k, cudaStream_t s, Scratch &scratch, uint64_t **partial_out,
                     int *n_split_out, const TuneCfg *cfg)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false>, (int)smem_bytes(MODE_PLAIN)));
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, true>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false, false>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, true, true>, (int)smem_bytes(MODE_PLAIN)));
     const int n_mtiles = (int)((nq + TM - 1) / TM);
     const int n_mpairs = (n_mtiles + QT - 1) / QT;
     const int64_t n_ntiles = (n + TN - 1) / TN;
@@ -1094,7 +1111,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
         if (pre)
             DT_CUDA_TRY(launch_pre<MODE_PLAIN>(a, 2 * (int64_t)a.n_mpairs * n_split, s));
         else
-            bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
+            bf_tc_kernel<MODE_PLAIN, false, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
         DT_CUDA_TRY(cudaGetLastError());
     }
     *partial_out = partial;
@@ -1116,9 +1133,10 @@ int take_tc_error(bool *raised)
 int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
                     const int32_t *slot_q, const TcUnit *units, const int64_t *n_units,
                     const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
-                    cudaStream_t s)
+                    cudaStream_t s, const unsigned char *b_exp, const uint32_t *b_side)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false, false>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, true, false>, (int)smem_bytes(MODE_PLAIN)));
     if (max_tiles <= 0) return DT_OK;
     unsigned char *a_exp = nullptr;
     uint32_t *qpop = nullptr, *err = nullptr;
@@ -1143,10 +1161,64 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.partial = partial;
     a.err = err;
     const int grid = (int)std::min<int64_t>(max_tiles, sm_count());   // units <= tiles
-    bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
+    if (b_exp) {
+        a.b_exp = b_exp;
+        a.b_side = b_side;
+        bf_tc_kernel<MODE_PLAIN, true, false><<<grid, kernel_threads(true), smem_bytes(MODE_PLAIN), s>>>(a);
+    } else {
+        bf_tc_kernel<MODE_PLAIN, false, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
+    }
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
+
+namespace {
+// Tiles t of rows [tile_row0[t], tile_row1[t]) (at most 128) -> stage images
+// and per-row |t| (rows past the range: zero bits).
+__global__ void widen_tiles_kernel(const uint64_t *__restrict__ db, const int64_t *__restrict__ tile_row0,
+                                   const int64_t *__restrict__ tile_row1, int64_t n_tiles,
+                                   unsigned char *__restrict__ b_exp, uint32_t *__restrict__ rowpop)
+{
+    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (tile, row, chunk)
+    if (id >= n_tiles * TN * NCHUNK) return;
+    const int c = (int)(id % NCHUNK);
+    const int row = (int)((id / NCHUNK) % TN);
+    const int64_t t = id / ((int64_t)NCHUNK * TN);
+    const int64_t src = tile_row0[t] + row;
+    const bool has = src < tile_row1[t];
+    uint4 bits = make_uint4(0, 0, 0, 0);
+    if (has) bits = __ldg(reinterpret_cast<const uint4 *>(db + src * kWords) + c);
+    store_row_chunk(b_exp + ((size_t)t * NCHUNK + c) * B_STAGE, row, bits);
+    if (c == 0) {
+        uint32_t sum = 0;
+        if (has) {
+            const uint4 *r = reinterpret_cast<const uint4 *>(db + src * kWords);
+            for (int j = 0; j < NCHUNK; ++j) {
+                const uint4 v = __ldg(r + j);
+                sum += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            }
+        }
+        rowpop[t * TN + row] = sum;
+    }
+}
+}  // namespace
+
+int widen_tiles_into(const uint64_t *db, const int64_t *tile_row0, const int64_t *tile_row1,
+                     int64_t n_tiles, unsigned char *b_exp, uint32_t *b_side, cudaStream_t s)
+{
+    if (n_tiles <= 0) return DT_OK;
+    Scratch scratch(s);
+    uint32_t *rowpop = nullptr;
+    DT_CUDA_TRY(scratch.alloc(&rowpop, (size_t)n_tiles * TN * 4));
+    const int64_t items = n_tiles * TN * NCHUNK;
+    widen_tiles_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(db, tile_row0, tile_row1, n_tiles,
+                                                                        b_exp, rowpop);
+    side_kernel<<<(unsigned)n_tiles, TN, 0, s>>>(rowpop, n_tiles * TN, b_side);
+    DT_CUDA_TRY(cudaGetLastError());
+    return DT_OK;
+}
+
+size_t tc_side_bytes() { return SIDE_BYTES; }
 
 size_t tc_tile_bytes() { return (size_t)NCHUNK * A_STAGE; }
 
@@ -1166,7 +1238,7 @@ int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
                         const int64_t *n_units, int64_t max_units, int k, uint64_t *partial,
                         cudaStream_t s)
 {
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false>, (int)smem_bytes(MODE_PLAIN)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false, false>, (int)smem_bytes(MODE_PLAIN)));
     if (max_units <= 0) return DT_OK;
     uint32_t *err = nullptr;
     DT_CUDA_TRY(cudaGetSymbolAddress((void **)&err, g_tc_error));
@@ -1183,7 +1255,7 @@ int launch_tc_units_pre(const uint64_t *db, int64_t n, const uint32_t *idx_map,
     a.partial = partial;
     a.err = err;
     const int grid = (int)std::min<int64_t>(2 * max_units, sm_count());
-    bf_tc_kernel<MODE_PLAIN, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
+    bf_tc_kernel<MODE_PLAIN, false, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
@@ -1194,9 +1266,9 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
                    int64_t *need_words_out)
 {
     static_assert(TN == kScanTileRows, "scan tiles are tensor-core tiles");
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_BOUND, false>, (int)smem_bytes(MODE_BOUND)));
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_TREE, false>, (int)smem_bytes(MODE_TREE)));
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_TREE, true>, (int)smem_bytes(MODE_TREE)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_BOUND, false, false>, (int)smem_bytes(MODE_BOUND)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_TREE, false, false>, (int)smem_bytes(MODE_TREE)));
+    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_TREE, true, true>, (int)smem_bytes(MODE_TREE)));
     const int64_t n = ix->n;
     const int64_t n_tt = (n + TN - 1) / TN;             // scan tiles
     const int64_t need_words = (n_tt + 31) / 32;
@@ -1241,7 +1313,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
         b.mp_base = p0;
         b.n_mpairs = std::min(kBatchPairs, n_mpairs - p0);
         KernelTimer timer("tree_bound", s);
-        bf_tc_kernel<MODE_BOUND, false><<<(int)std::min<int64_t>(2 * (int64_t)b.n_mpairs * b.n_split, sms),
+        bf_tc_kernel<MODE_BOUND, false, false><<<(int)std::min<int64_t>(2 * (int64_t)b.n_mpairs * b.n_split, sms),
                                            kernel_threads(false), smem_bytes(MODE_BOUND), s>>>(b);
     }
     DT_CUDA_TRY(cudaGetLastError());
@@ -1298,7 +1370,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
         if (pre)
             DT_CUDA_TRY(launch_pre<MODE_TREE>(a, 2 * (int64_t)a.n_mpairs * a.n_split, s));
         else
-            bf_tc_kernel<MODE_TREE, false><<<grid, kernel_threads(false), smem_bytes(MODE_TREE), s>>>(a);
+            bf_tc_kernel<MODE_TREE, false, false><<<grid, kernel_threads(false), smem_bytes(MODE_TREE), s>>>(a);
         DT_CUDA_TRY(cudaGetLastError());
     }
     DT_CUDA_TRY(cudaGetLastError());

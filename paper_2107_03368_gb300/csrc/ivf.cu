@@ -370,7 +370,8 @@ __global__ void pair_count_kernel(const int32_t *__restrict__ probe, int64_t pai
 // One block: per list, ceil(count / 128) query tiles (numbered list by
 // list from tile_base) and ceil(tiles / 2) units of up to two tiles each.
 __global__ void unit_plan_kernel(const int32_t *__restrict__ counts, int K,
-                                 const int64_t *__restrict__ offsets, int64_t *__restrict__ tile_base,
+                                 const int64_t *__restrict__ offsets, const int64_t *__restrict__ wbase,
+                                 int64_t *__restrict__ tile_base,
                                  TcUnit *__restrict__ units, int64_t *__restrict__ n_units,
                                  int64_t *__restrict__ n_tiles)
 {
@@ -397,6 +398,7 @@ __global__ void unit_plan_kernel(const int32_t *__restrict__ counts, int K,
                 u.a_tile1 = two ? (int32_t)(t0 + 2 * i + 1) : -1;
                 u.nvalid1 = two ? (int32_t)min(cnt - (2 * i + 1) * kTcTileM, (uint32_t)kTcTileM) : 0;
                 u.out_base = 0;
+                u.tile0 = wbase ? wbase[c] : 0;
                 units[u0 + i] = u;
             }
         }
@@ -476,7 +478,71 @@ struct dt_ivf {
     int64_t *offsets = nullptr;     // [K+1]
     uint64_t *db = nullptr;         // [n][64] cluster order
     uint32_t *ids = nullptr;        // [n] original index
+    // Optional: the list-ordered rows widened for the tensor-core scan, each
+    // list starting on a tile of 128 rows (its last tile zero-padded): list
+    // c's rows offsets[c] + 128 i .. are tile wbase[c] + i.  Null when the
+    // copy did not fit at build time.
+    int64_t *wbase = nullptr;       // [K] (device)
+    unsigned char *w_exp = nullptr; // [w_tiles][tc_tile_bytes()]
+    uint32_t *w_side = nullptr;     // [w_tiles][tc_side_bytes() / 4]
+    int64_t w_tiles = 0;
 };
+
+namespace {
+void free_widened(dt_ivf *ix)
+{
+    cudaFree(ix->wbase);
+    cudaFree(ix->w_exp);
+    cudaFree(ix->w_side);
+    ix->wbase = nullptr;
+    ix->w_exp = nullptr;
+    ix->w_side = nullptr;
+    ix->w_tiles = 0;
+}
+
+// Build the widened copy when it fits in half the free device memory; on
+// any failure leave it out (the scan then widens rows itself).
+void build_widened(dt_ivf *ix, cudaStream_t s)
+{
+    std::vector<int64_t> off((size_t)ix->K + 1), wb((size_t)ix->K), r0, r1;
+    if (cudaMemcpy(off.data(), ix->offsets, off.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    for (int c = 0; c < ix->K; ++c) {
+        wb[c] = (int64_t)r0.size();
+        for (int64_t r = off[c]; r < off[c + 1]; r += 128) {
+            r0.push_back(r);
+            r1.push_back(off[c + 1]);
+        }
+    }
+    const int64_t T = (int64_t)r0.size();
+    size_t free_b = 0, total_b = 0;
+    if (T == 0 || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const size_t need = (size_t)T * (dtk::tc_tile_bytes() + dtk::tc_side_bytes() + 16) + (size_t)ix->K * 8;
+    if (need > free_b / 2) return;
+    int64_t *d_r = nullptr;
+    bool ok = cudaMalloc((void **)&ix->wbase, (size_t)ix->K * 8) == cudaSuccess &&
+              cudaMalloc((void **)&ix->w_exp, (size_t)T * dtk::tc_tile_bytes()) == cudaSuccess &&
+              cudaMalloc((void **)&ix->w_side, (size_t)T * dtk::tc_side_bytes()) == cudaSuccess &&
+              cudaMalloc((void **)&d_r, (size_t)T * 16) == cudaSuccess;
+    ok = ok && cudaMemcpy(ix->wbase, wb.data(), (size_t)ix->K * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(d_r, r0.data(), (size_t)T * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(d_r + T, r1.data(), (size_t)T * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && dtk::widen_tiles_into(ix->db, d_r, d_r + T, T, ix->w_exp, ix->w_side, s) == DT_OK &&
+         cudaStreamSynchronize(s) == cudaSuccess;
+    cudaFree(d_r);
+    if (!ok) {
+        cudaGetLastError();
+        free_widened(ix);
+        return;
+    }
+    ix->w_tiles = T;
+}
+}  // namespace
 
 using namespace dtk;
 
@@ -547,6 +613,7 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
         delete ix;
         return rc;
     }
+    build_widened(ix, s);
     *out = ix;
     return DT_OK;
 }
@@ -557,6 +624,7 @@ void ivf_free(dt_ivf *ix)
     cudaDeviceSynchronize();
     cudaFree(ix->cent); cudaFree(ix->cent_t); cudaFree(ix->offsets); cudaFree(ix->db);
     cudaFree(ix->ids);
+    free_widened(ix);
     delete ix;
 }
 
@@ -632,12 +700,12 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     }
     const unsigned pb = (unsigned)std::min<int64_t>((pairs + 255) / 256, 8192);
     pair_count_kernel<<<pb, 256, 0, s>>>(probe, pairs, counts);
-    unit_plan_kernel<<<1, 1024, 0, s>>>(counts, ix->K, ix->offsets, tile_base, units, n_units,
-                                        n_tiles);
+    unit_plan_kernel<<<1, 1024, 0, s>>>(counts, ix->K, ix->offsets, ix->wbase, tile_base, units,
+                                        n_units, n_tiles);
     pair_scatter_kernel<<<pb, 256, 0, s>>>(probe, nq, n_probe, tile_base, fill, slot_q, slot_of);
     DT_CUDA_TRY(cudaGetLastError());
     int rc = launch_tc_units(ix->db, ix->n, ix->ids, d_q, slot_q, units, n_units, n_tiles,
-                             max_tiles, k, partial, s);
+                             max_tiles, k, partial, s, ix->w_exp, ix->w_side);
     if (rc == DT_OK) {
         pair_merge_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(partial, slot_of, n_probe, d_q,
                                                                    nq, k, d_idx, d_score);
