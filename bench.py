@@ -493,10 +493,11 @@ def run_ours(a, dist):
     return 0
 
 
-# kernels of this library launched by one batched dt_search call: descent,
-# 3 radix passes x 3 kernels, slots, query widening, bound pass, database
-# widening (2), scan, merge
-LAUNCHES_PER_TREE_SEARCH = 17
+# kernels of this library launched by one batched dt_search call (one
+# batch of query tiles): descent, 3 radix passes x 3 kernels, slots, query
+# widening, bound pass, scan, merge; the database widening (2 more) is not
+# launched when the index keeps its widened copy, as the headline leg's does
+LAUNCHES_PER_TREE_SEARCH = 15
 
 
 def top1_leg(a, dt, ix, d_db, d_q, stream):
