@@ -1001,6 +1001,27 @@ bool want_prewiden(int64_t n, int64_t nq, int forced)
     return bytes <= free_b / 2;
 }
 
+// Database splits for `per` units per split on `ctas` persistent CTAs that
+// take units round-robin: the fewest splits whose units fill the last wave
+// best, so that every CTA runs the same number of units (10M x 10k top-10:
+// 19 splits, ten full waves, 5% faster than 7 splits and a 92% last wave);
+// at most 64 splits and at least 8 tiles (4 steps) per split.
+int pick_tc_splits(int64_t per, int64_t n_tiles, int ctas)
+{
+    const int max_s = (int)std::max<int64_t>(1, std::min<int64_t>(64, n_tiles / 8));
+    int best = 1;
+    double best_eff = -1.0;
+    for (int sp = 1; sp <= max_s; ++sp) {
+        const double waves = (double)per * sp / ctas;
+        const double eff = waves / std::ceil(waves);
+        if (eff > best_eff + 0.004) {
+            best_eff = eff;
+            best = sp;
+        }
+    }
+    return best;
+}
+
 // Tiles per split when n_tiles tiles are cut into `splits` splits, rounded
 // up to whole steps so that no split ends with a half-empty step.
 int64_t step_tiles(int64_t n_tiles, int splits)
@@ -1057,7 +1078,7 @@ int tc_partial_topk(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     const bool pre = want_prewiden(n, nq, c.b);
     const int batch_pairs = std::min(n_mpairs, kBatchPairs);
     const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_ntiles)
-                               : pick_bf_splits(2 * batch_pairs, n_ntiles, sms);
+                               : pick_tc_splits(2 * batch_pairs, n_ntiles, sms);
     const int64_t tiles_per_split = step_tiles(n_ntiles, splits);
     const int n_split = (int)((n_ntiles + tiles_per_split - 1) / tiles_per_split);
 
@@ -1301,7 +1322,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     b.n_ntiles = (n_tt + TN - 1) / TN;
     const int batch_pairs = std::min(n_mpairs, kBatchPairs);
     {
-        const int splits = pick_bf_splits(2 * batch_pairs, b.n_ntiles, sms);
+        const int splits = pick_tc_splits(2 * batch_pairs, b.n_ntiles, sms);
         b.tiles_per_split = step_tiles(b.n_ntiles, splits);
         b.n_split = (int)((b.n_ntiles + b.tiles_per_split - 1) / b.tiles_per_split);
     }
@@ -1332,7 +1353,7 @@ int launch_tree_tc(const dt_index *ix, const uint64_t *q, int64_t nq, const int3
     a.n_ntiles = n_tt;
     TuneCfg c{0, 0};
     tune_lookup(TUNE_TREE_TC, n, nq, k, &c);
-    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_tt) : pick_bf_splits(2 * batch_pairs, n_tt, sms);
+    const int splits = c.a > 0 ? (int)std::min<int64_t>(c.a, n_tt) : pick_tc_splits(2 * batch_pairs, n_tt, sms);
     a.tiles_per_split = step_tiles(n_tt, splits);
     a.n_split = (int)((n_tt + a.tiles_per_split - 1) / a.tiles_per_split);
     a.need = need;
