@@ -227,9 +227,9 @@ def fp8_peak(sustained):
 # capture of a smaller case (the command is in
 # profiles/tree_scan_1M_10k.md): at a fixed query batch every split of the
 # database is streamed by the CTAs of its wave, so the bytes grow with the
-# database rows; scaled to a launch by n.  (85.63 GB read + 0.175 GB written
-# at 1M rows; recapture when the scan kernel changes.)
-TREE_SCAN_TRAFFIC = {"bytes_per_row": 85803.0, "rows": 1_000_000, "queries": 10_000, "k": 10}
+# database rows; scaled to a launch by n.  (109.93 GB read + 0.203 GB written
+# at 1M rows; recapture when the scan kernel or its launch shape changes.)
+TREE_SCAN_TRAFFIC = {"bytes_per_row": 110135.0, "rows": 1_000_000, "queries": 10_000, "k": 10}
 
 
 def tree_scan_traffic(a):
