@@ -251,11 +251,15 @@ int dt_export(const dt_index *index, int64_t *h_child, int64_t *h_begin, int64_t
  * strictly greater than a key known to be >= the query's k-th result's
  * A*Z + B*P, so the result equals bf_search's, ties included.
  *
- * Two traversals, chosen by batch size (dt_search_path picks explicitly):
- *   per query (fewer than 64 queries): a warp per query walks the tree
+ * Two traversals, chosen by batch and index size (dt_search_path picks
+ * explicitly):
+ *   per query (fewer than 64 queries on an index of fewer than 131,072
+ *     descriptors): a warp per query walks the tree
  *     depth first with the bound of every node (dt_stats counts its nodes,
  *     leaves, descriptors and bounds);
- *   batched (64 or more): every query first descends greedily to one leaf
+ *   batched (64 or more queries, or any batch on a larger index, where one
+ *     warp walking most of the rows would take far longer than one shared
+ *     scan): every query first descends greedily to one leaf
  *     and scans it, which gives a cap >= its k-th key; queries are sorted
  *     by the position of that leaf and grouped 256 at a time; the tensor
  *     cores bound every (group, run of 128 tree-ordered rows) by the run's

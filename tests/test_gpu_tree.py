@@ -282,3 +282,21 @@ def test_kept_widened_copy_follows_insertion():
     idx, score, ab, _ = dt.dt_search_path(ix, to_dev(q), 7, 2, with_ab=True)
     pick = np.unique(np.linspace(0, q.shape[0] - 1, 120).astype(np.int64))
     assert_matches_oracle(db, q[pick], 7, idx[pick], score[pick], ab[pick])
+
+
+def test_small_batches_on_a_large_index_take_the_batched_traversal():
+    """On an index of 2^17 descriptors or more, dt_search scans batched even
+    for a handful of queries (one warp walking most of the rows alone takes
+    far longer): its counters are the batched traversal's, and its results
+    equal the per-query walk's and the oracle's."""
+    db = mixed_db(97, 140_000, per_object=500)
+    q = edge_queries(98, db, 10)
+    d_q = to_dev(q)
+    ix = dt.dt_build(to_dev(db))
+    auto = dt.dt_search(ix, d_q, 6, with_ab=True, stats=True)
+    batched = dt.dt_search_path(ix, d_q, 6, 2, with_ab=True, stats=True)
+    walk = dt.dt_search_path(ix, d_q, 6, 1, with_ab=True)
+    for a, b, c in zip(auto[:3], batched[:3], walk[:3]):
+        assert torch_equal(a, b) and torch_equal(a, c)
+    assert auto[3] == batched[3]
+    assert_matches_oracle(db, q, 6, auto[0], auto[1], auto[2])
