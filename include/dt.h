@@ -390,7 +390,9 @@ int bf_search_noalloc(const uint64_t *d_db, int64_t n, const uint64_t *d_q, int6
  *   launch; 2 = tensor-core scan of the index's whole database; 3 = the
  *   batched tree search of dt_search (descriptors of one partial query
  *   share leaves, so their groups skip most of the database); 0 =
- *   automatic (3 when n_qdesc >= 256, else 1).  With T > 0, engines 2 and
+ *   automatic (dt_autotune_retrieve's choice when tuned, else 3 when
+ *   n_qdesc >= 256 or the index holds 131,072 descriptors or more, else
+ *   1).  With T > 0, engines 2 and
  *   3 search the draws in rounds of T, 2T, ... per undecided query, so
  *   mostly only the draws the loop consumes are searched.
  * With T = 0 the call does not synchronise the stream; with T > 0 and

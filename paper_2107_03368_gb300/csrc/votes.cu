@@ -420,7 +420,11 @@ int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects
     TuneCfg c{0, 0};
     if (cfg) c = *cfg;
     else tune_lookup(TUNE_RETRIEVE, ix->n, threshold > 0 ? 2 : 1, 1, &c);
-    if (engine == 0) engine = c.a >= 1 && c.a <= 3 ? c.a : (total >= 256 ? 3 : 1);
+    // untuned: the batched search from 256 query descriptors, or on a large
+    // index, where a warp walking most of the rows per descriptor is slow
+    // whatever the batch (as in dt_search)
+    if (engine == 0)
+        engine = c.a >= 1 && c.a <= 3 ? c.a : (total >= 256 || ix->n >= (int64_t(1) << 17) ? 3 : 1);
     if (engine >= 2)
         return retrieve_batched(ix, object_of, n_objects, qdesc, qoffsets, nq, total, threshold,
                                 seed, votes, winner, consumed, engine == 3, s);
