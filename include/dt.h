@@ -65,7 +65,7 @@ enum {
     DT_ENOMEM = -2,        /* device allocation failed */
     DT_ECUDA = -3,         /* a CUDA runtime call failed */
     DT_ETIMEOUT = -4,      /* a bounded device wait gave up */
-    DT_EUNSUPPORTED = -5,  /* valid request this build/device cannot serve */
+    DT_EUNSUPPORTED = -5,  /* valid request this library or device cannot serve */
     DT_EIO = -6            /* a file could not be opened, read or written */
 };
 
