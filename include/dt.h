@@ -519,11 +519,9 @@ int enc_train_step(dt_encoder *enc, const uint64_t *d_q, const uint64_t *d_t, in
 
 /* Inverted file over the encoder's embeddings of a database: k-means with
  * n_lists cosine centroids (iters Lloyd iterations from evenly spaced
- * seeds), the database copied list by list.  When it fits in half the free
- * device memory the index also keeps the list-ordered rows widened for the
- * tensor cores (about 4 KB per descriptor plus up to 512 KB per list), which
- * the list-major search then reads instead of widening rows per call.
- * Synchronises `stream`. */
+ * seeds), the database copied list by list.  The centroid sums are exact
+ * fixed-point integers, so the same encoder and database give the same
+ * lists on every run.  n < 2^32.  Synchronises `stream`. */
 typedef struct dt_ivf dt_ivf;
 int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_lists,
               int32_t iters, void *stream, dt_ivf **out);

@@ -362,10 +362,13 @@ template <bool LOCK = false>
 __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
 {
     Unit v;
-    const int64_t pu = u >> 1;
-    const int qh = (int)(u & 1);
     if (a.units) {
-        const TcUnit t = a.units[pu];
+        // list units: the first tiles of all units, then the second ones
+        // (mostly absent), so that the CTAs, which take units round-robin,
+        // all get present tiles whatever the parity of the grid
+        const int64_t nu = __ldg(a.n_units);
+        const int qh = u >= nu ? 1 : 0;
+        const TcUnit t = a.units[qh ? u - nu : u];
         v.mt = qh ? t.a_tile1 : t.a_tile0;
         v.mt_a = v.mt;
         v.nvalid = qh ? t.nvalid1 : t.nvalid0;
@@ -373,9 +376,11 @@ __device__ __forceinline__ Unit get_unit(const TcArgs &a, int64_t u)
         v.r1 = t.row1;
         v.sp = 0;
         v.mp = 0;
-        v.t0 = t.tile0;
+        v.t0 = 0;
         v.out_base = t.out_base;
     } else {
+        const int64_t pu = u >> 1;
+        const int qh = (int)(u & 1);
         const int64_t mp = a.mp_base + pu % a.n_mpairs;
         v.sp = pu / a.n_mpairs;
         v.mp = mp;
@@ -501,9 +506,9 @@ __device__ __noinline__ uint64_t list_insert(uint64_t *L, int k, uint32_t key, i
     return L[k - 1];
 }
 
-// PRE: database chunks arrive pre-widened by bulk copies; CL (split mode,
-// implies PRE): the two CTAs of a cluster hold a pair's two query tiles and
-// multicast the database chunks to each other.
+// PRE: database chunks arrive pre-widened by bulk copies, and CL: the two
+// CTAs of a cluster hold a pair's two query tiles and multicast the database
+// chunks to each other (split mode; the two always go together).
 template <int MODE, bool PRE, bool CL>
 __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcArgs args)
 {
@@ -520,7 +525,7 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
     uint32_t *err = args.err;
 
     constexpr int EPI = epi_warps(PRE), MMAW = mma_warp(PRE);
-    static_assert(PRE || !CL, "clusters share pre-widened chunks");
+    static_assert(PRE == CL, "pre-widened chunks are shared by the CTA pairs");
     // slice groups: one per 4 epilogue warps, each with its own list per
     // query; in list mode (one list per slot) a single group, except for
     // k = 1, where the groups merge into the slot's entry by atomic minimum
@@ -588,20 +593,11 @@ __global__ void __launch_bounds__(kernel_threads(PRE), 1) bf_tc_kernel(const TcA
                         unsigned char *dst = smem + (size_t)s * STAGE;
                         bulk_g2s_hint(dst, args.a_exp + ((size_t)uv.mt_a * NCHUNK + c) * A_STAGE,
                                       (uint32_t)A_STAGE, &ctl->full[s], keep);
-                        if (CL) {
-                            const int64_t gt = rank ? gt1 : gt0;
-                            if (gt >= 0)
-                                bulk_g2s_mc_hint(dst + A_STAGE + rank * B_STAGE,
-                                                 args.b_exp + ((size_t)gt * NCHUNK + c) * B_STAGE,
-                                                 (uint32_t)B_STAGE, &ctl->full[s], 0x3, stream);
-                        } else {
-                            bulk_g2s_hint(dst + A_STAGE, args.b_exp + ((size_t)gt0 * NCHUNK + c) * B_STAGE,
-                                          (uint32_t)B_STAGE, &ctl->full[s], stream);
-                            if (gt1 >= 0)
-                                bulk_g2s_hint(dst + A_STAGE + B_STAGE,
-                                              args.b_exp + ((size_t)gt1 * NCHUNK + c) * B_STAGE,
-                                              (uint32_t)B_STAGE, &ctl->full[s], stream);
-                        }
+                        const int64_t gt = rank ? gt1 : gt0;
+                        if (gt >= 0)
+                            bulk_g2s_mc_hint(dst + A_STAGE + rank * B_STAGE,
+                                             args.b_exp + ((size_t)gt * NCHUNK + c) * B_STAGE,
+                                             (uint32_t)B_STAGE, &ctl->full[s], 0x3, stream);
                         if (c == last_c) {
                             bulk_g2s_hint(slot, args.b_side + (size_t)gt0 * SIDE_WORDS, SIDE_BYTES,
                                           &ctl->full[s], stream);
@@ -1154,10 +1150,9 @@ int take_tc_error(bool *raised)
 int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
                     const int32_t *slot_q, const TcUnit *units, const int64_t *n_units,
                     const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
-                    cudaStream_t s, const unsigned char *b_exp, const uint32_t *b_side)
+                    cudaStream_t s)
 {
     DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, false, false>, (int)smem_bytes(MODE_PLAIN)));
-    DT_CUDA_TRY(allow_smem((const void *)bf_tc_kernel<MODE_PLAIN, true, false>, (int)smem_bytes(MODE_PLAIN)));
     if (max_tiles <= 0) return DT_OK;
     unsigned char *a_exp = nullptr;
     uint32_t *qpop = nullptr, *err = nullptr;
@@ -1182,64 +1177,10 @@ int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, cons
     a.partial = partial;
     a.err = err;
     const int grid = (int)std::min<int64_t>(max_tiles, sm_count());   // units <= tiles
-    if (b_exp) {
-        a.b_exp = b_exp;
-        a.b_side = b_side;
-        bf_tc_kernel<MODE_PLAIN, true, false><<<grid, kernel_threads(true), smem_bytes(MODE_PLAIN), s>>>(a);
-    } else {
-        bf_tc_kernel<MODE_PLAIN, false, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
-    }
+    bf_tc_kernel<MODE_PLAIN, false, false><<<grid, kernel_threads(false), smem_bytes(MODE_PLAIN), s>>>(a);
     DT_CUDA_TRY(cudaGetLastError());
     return DT_OK;
 }
-
-namespace {
-// Tiles t of rows [tile_row0[t], tile_row1[t]) (at most 128) -> stage images
-// and per-row |t| (rows past the range: zero bits).
-__global__ void widen_tiles_kernel(const uint64_t *__restrict__ db, const int64_t *__restrict__ tile_row0,
-                                   const int64_t *__restrict__ tile_row1, int64_t n_tiles,
-                                   unsigned char *__restrict__ b_exp, uint32_t *__restrict__ rowpop)
-{
-    const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (tile, row, chunk)
-    if (id >= n_tiles * TN * NCHUNK) return;
-    const int c = (int)(id % NCHUNK);
-    const int row = (int)((id / NCHUNK) % TN);
-    const int64_t t = id / ((int64_t)NCHUNK * TN);
-    const int64_t src = tile_row0[t] + row;
-    const bool has = src < tile_row1[t];
-    uint4 bits = make_uint4(0, 0, 0, 0);
-    if (has) bits = __ldg(reinterpret_cast<const uint4 *>(db + src * kWords) + c);
-    store_row_chunk(b_exp + ((size_t)t * NCHUNK + c) * B_STAGE, row, bits);
-    if (c == 0) {
-        uint32_t sum = 0;
-        if (has) {
-            const uint4 *r = reinterpret_cast<const uint4 *>(db + src * kWords);
-            for (int j = 0; j < NCHUNK; ++j) {
-                const uint4 v = __ldg(r + j);
-                sum += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-            }
-        }
-        rowpop[t * TN + row] = sum;
-    }
-}
-}  // namespace
-
-int widen_tiles_into(const uint64_t *db, const int64_t *tile_row0, const int64_t *tile_row1,
-                     int64_t n_tiles, unsigned char *b_exp, uint32_t *b_side, cudaStream_t s)
-{
-    if (n_tiles <= 0) return DT_OK;
-    Scratch scratch(s);
-    uint32_t *rowpop = nullptr;
-    DT_CUDA_TRY(scratch.alloc(&rowpop, (size_t)n_tiles * TN * 4));
-    const int64_t items = n_tiles * TN * NCHUNK;
-    widen_tiles_kernel<<<(unsigned)((items + 255) / 256), 256, 0, s>>>(db, tile_row0, tile_row1, n_tiles,
-                                                                        b_exp, rowpop);
-    side_kernel<<<(unsigned)n_tiles, TN, 0, s>>>(rowpop, n_tiles * TN, b_side);
-    DT_CUDA_TRY(cudaGetLastError());
-    return DT_OK;
-}
-
-size_t tc_side_bytes() { return SIDE_BYTES; }
 
 size_t tc_tile_bytes() { return (size_t)NCHUNK * A_STAGE; }
 

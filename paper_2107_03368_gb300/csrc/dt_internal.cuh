@@ -368,35 +368,21 @@ int launch_retrieve(const dt_index *ix, const uint32_t *object_of, int n_objects
 // Work unit of the tensor-core scan in list mode: the query tiles a_tile0
 // and a_tile1 (TM rows each, the first nvalid0 / nvalid1 of them real;
 // a_tile1 < 0: none) against database rows [row0, row1).  Results go to
-// partial[a_tile * TM + row][k].  With a widened copy of the rows
-// (launch_tc_units with b_exp), rows row0 + 128 i .. of the unit are its
-// tile tile0 + i there.
+// partial[a_tile * TM + row][k].
 struct TcUnit {
     int64_t row0, row1;
     int32_t a_tile0, a_tile1, nvalid0, nvalid1;
     int64_t out_base;    // added to the slot: results go to partial[out_base + slot][k]
-    int64_t tile0;       // first tile of the rows in the widened copy (unused without one)
 };
 // Tensor-core scan over a unit table built on the device: *n_units units
 // covering *n_tiles query tiles (at most max_tiles); the row r of tile t is
 // query slot_q[t * TM + r] (negative = padding).  Rows are reported through
-// idx_map.
-// b_exp / b_side (nullable): a widened, tile-aligned copy of the rows (see
-// widen_tiles_into); the scan then reads it by bulk copies instead of
-// widening the rows itself.  For k = 1 the slot's entry is merged with an
-// atomic minimum (partial must start at all ones, as always).
+// idx_map.  For k = 1 the slot's entry is merged with an atomic minimum
+// (partial must start at all ones, as always).
 int launch_tc_units(const uint64_t *db, int64_t n, const uint32_t *idx_map, const uint64_t *q,
                     const int32_t *slot_q, const TcUnit *units, const int64_t *n_units,
                     const int64_t *n_tiles, int64_t max_tiles, int k, uint64_t *partial,
-                    cudaStream_t s, const unsigned char *b_exp = nullptr,
-                    const uint32_t *b_side = nullptr);
-// Widen n_tiles tiles of 128 rows for the tensor-core scan: tile t holds
-// rows tile_row0[t] .. min(tile_row0[t] + 128, tile_row1[t]) - 1 of db, the
-// rest of the tile zero.  b_exp [n_tiles][tc_tile_bytes()], b_side
-// [n_tiles][tc_side_bytes()] are the caller's.
-int widen_tiles_into(const uint64_t *db, const int64_t *tile_row0, const int64_t *tile_row1,
-                     int64_t n_tiles, unsigned char *b_exp, uint32_t *b_side, cudaStream_t s);
-size_t tc_side_bytes();      // bytes of one tile's |t| record
+                    cudaStream_t s);
 constexpr int kTcTileM = 128;
 // Queries -> pre-widened tensor-core tiles a_exp [ceil(nq/128)][32 chunks][16 KB]
 // and |q| (qpop [ceil(nq/128) * 128]); both device buffers of the caller.

@@ -87,10 +87,16 @@ assign_kernel(const __nv_bfloat16 *__restrict__ emb, int64_t n, const float *__r
     if (tid < KT && p0 + tid < n) assign[p0 + tid] = (int32_t)(0xFFFFFFFFu - (uint32_t)(best[tid] & 0xFFFFFFFFu));
 }
 
+// Centroid sums in fixed point: each component (|x| <= 1, the embeddings
+// are unit length) scaled by 2^30 and rounded to an integer, so that the
+// sums, integer additions, do not depend on the order of the atomics and the
+// build is the same on every run.  2^30 * n stays below 2^63 for n < 2^32.
+constexpr float kSumScale = 1073741824.f;   // 2^30
+
 // sums[c] += emb[i] for assign[i] = c; counts[c] += 1
 __global__ void accumulate_kernel(const __nv_bfloat16 *__restrict__ emb, int64_t n,
-                                  const int32_t *__restrict__ assign, float *__restrict__ sums,
-                                  int32_t *__restrict__ counts)
+                                  const int32_t *__restrict__ assign,
+                                  unsigned long long *__restrict__ sums, int32_t *__restrict__ counts)
 {
     const int lane = threadIdx.x & 31;
     int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -99,13 +105,14 @@ __global__ void accumulate_kernel(const __nv_bfloat16 *__restrict__ emb, int64_t
         const int c = assign[i];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            atomicAdd(&sums[(int64_t)c * D + lane + 32 * j], __bfloat162float(emb[i * D + lane + 32 * j]));
+            atomicAdd(&sums[(int64_t)c * D + lane + 32 * j],
+                      (unsigned long long)__float2ll_rn(__bfloat162float(emb[i * D + lane + 32 * j]) * kSumScale));
         if (lane == 0) atomicAdd(&counts[c], 1);
     }
 }
 
 // centroid = normalised sum (kept when its cluster is empty); warp per centroid
-__global__ void update_kernel(const float *__restrict__ sums, const int32_t *__restrict__ counts,
+__global__ void update_kernel(const unsigned long long *__restrict__ sums, const int32_t *__restrict__ counts,
                               int K, float *__restrict__ cent)
 {
     const int lane = threadIdx.x & 31;
@@ -114,7 +121,7 @@ __global__ void update_kernel(const float *__restrict__ sums, const int32_t *__r
     float v[4], ss = 0.f;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        v[j] = sums[(int64_t)c * D + lane + 32 * j];
+        v[j] = __ll2float_rn((long long)sums[(int64_t)c * D + lane + 32 * j]) / kSumScale;
         ss += v[j] * v[j];
     }
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
@@ -370,8 +377,7 @@ __global__ void pair_count_kernel(const int32_t *__restrict__ probe, int64_t pai
 // One block: per list, ceil(count / 128) query tiles (numbered list by
 // list from tile_base) and ceil(tiles / 2) units of up to two tiles each.
 __global__ void unit_plan_kernel(const int32_t *__restrict__ counts, int K,
-                                 const int64_t *__restrict__ offsets, const int64_t *__restrict__ wbase,
-                                 int64_t *__restrict__ tile_base,
+                                 const int64_t *__restrict__ offsets, int64_t *__restrict__ tile_base,
                                  TcUnit *__restrict__ units, int64_t *__restrict__ n_units,
                                  int64_t *__restrict__ n_tiles)
 {
@@ -398,7 +404,6 @@ __global__ void unit_plan_kernel(const int32_t *__restrict__ counts, int K,
                 u.a_tile1 = two ? (int32_t)(t0 + 2 * i + 1) : -1;
                 u.nvalid1 = two ? (int32_t)min(cnt - (2 * i + 1) * kTcTileM, (uint32_t)kTcTileM) : 0;
                 u.out_base = 0;
-                u.tile0 = wbase ? wbase[c] : 0;
                 units[u0 + i] = u;
             }
         }
@@ -478,71 +483,7 @@ struct dt_ivf {
     int64_t *offsets = nullptr;     // [K+1]
     uint64_t *db = nullptr;         // [n][64] cluster order
     uint32_t *ids = nullptr;        // [n] original index
-    // Optional: the list-ordered rows widened for the tensor-core scan, each
-    // list starting on a tile of 128 rows (its last tile zero-padded): list
-    // c's rows offsets[c] + 128 i .. are tile wbase[c] + i.  Null when the
-    // copy did not fit at build time.
-    int64_t *wbase = nullptr;       // [K] (device)
-    unsigned char *w_exp = nullptr; // [w_tiles][tc_tile_bytes()]
-    uint32_t *w_side = nullptr;     // [w_tiles][tc_side_bytes() / 4]
-    int64_t w_tiles = 0;
 };
-
-namespace {
-void free_widened(dt_ivf *ix)
-{
-    cudaFree(ix->wbase);
-    cudaFree(ix->w_exp);
-    cudaFree(ix->w_side);
-    ix->wbase = nullptr;
-    ix->w_exp = nullptr;
-    ix->w_side = nullptr;
-    ix->w_tiles = 0;
-}
-
-// Build the widened copy when it fits in half the free device memory; on
-// any failure leave it out (the scan then widens rows itself).
-void build_widened(dt_ivf *ix, cudaStream_t s)
-{
-    std::vector<int64_t> off((size_t)ix->K + 1), wb((size_t)ix->K), r0, r1;
-    if (cudaMemcpy(off.data(), ix->offsets, off.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    for (int c = 0; c < ix->K; ++c) {
-        wb[c] = (int64_t)r0.size();
-        for (int64_t r = off[c]; r < off[c + 1]; r += 128) {
-            r0.push_back(r);
-            r1.push_back(off[c + 1]);
-        }
-    }
-    const int64_t T = (int64_t)r0.size();
-    size_t free_b = 0, total_b = 0;
-    if (T == 0 || cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-        cudaGetLastError();
-        return;
-    }
-    const size_t need = (size_t)T * (dtk::tc_tile_bytes() + dtk::tc_side_bytes() + 16) + (size_t)ix->K * 8;
-    if (need > free_b / 2) return;
-    int64_t *d_r = nullptr;
-    bool ok = cudaMalloc((void **)&ix->wbase, (size_t)ix->K * 8) == cudaSuccess &&
-              cudaMalloc((void **)&ix->w_exp, (size_t)T * dtk::tc_tile_bytes()) == cudaSuccess &&
-              cudaMalloc((void **)&ix->w_side, (size_t)T * dtk::tc_side_bytes()) == cudaSuccess &&
-              cudaMalloc((void **)&d_r, (size_t)T * 16) == cudaSuccess;
-    ok = ok && cudaMemcpy(ix->wbase, wb.data(), (size_t)ix->K * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(d_r, r0.data(), (size_t)T * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(d_r + T, r1.data(), (size_t)T * 8, cudaMemcpyHostToDevice) == cudaSuccess;
-    ok = ok && dtk::widen_tiles_into(ix->db, d_r, d_r + T, T, ix->w_exp, ix->w_side, s) == DT_OK &&
-         cudaStreamSynchronize(s) == cudaSuccess;
-    cudaFree(d_r);
-    if (!ok) {
-        cudaGetLastError();
-        free_widened(ix);
-        return;
-    }
-    ix->w_tiles = T;
-}
-}  // namespace
 
 using namespace dtk;
 
@@ -551,7 +492,8 @@ extern "C" {
 int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_lists, int32_t iters,
               void *stream, dt_ivf **out)
 {
-    DT_CHECK_ARG(enc && d_db && out && n >= 1 && n_lists >= 1 && n_lists <= n && iters >= 0,
+    DT_CHECK_ARG(enc && d_db && out && n >= 1 && n < (int64_t(1) << 32) && n_lists >= 1 &&
+                     n_lists <= n && iters >= 0,
                  "bad arguments");
     *out = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
@@ -562,7 +504,7 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
     ix->K = K;
     __nv_bfloat16 *emb = nullptr;
     int32_t *assign = nullptr, *counts = nullptr;
-    float *sums = nullptr;
+    unsigned long long *sums = nullptr;
     int rc = DT_OK;
     auto fail = [&](const char *what) {
         set_error(std::string("ivf_build: ") + what);
@@ -571,7 +513,7 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
     if (dt_malloc_async((void **)&emb, (size_t)n * D * 2, s) != cudaSuccess ||
         dt_malloc_async((void **)&assign, (size_t)n * 4, s) != cudaSuccess ||
         dt_malloc_async((void **)&counts, (size_t)K * 4, s) != cudaSuccess ||
-        dt_malloc_async((void **)&sums, (size_t)K * D * 4, s) != cudaSuccess ||
+        dt_malloc_async((void **)&sums, (size_t)K * D * 8, s) != cudaSuccess ||
         cudaMalloc((void **)&ix->cent, (size_t)K * D * 4) != cudaSuccess ||
         cudaMalloc((void **)&ix->cent_t, (size_t)K * D * 4) != cudaSuccess ||
         cudaMalloc((void **)&ix->offsets, (size_t)(K + 1) * 8) != cudaSuccess ||
@@ -587,7 +529,7 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
         for (int it = 0; it <= iters; ++it) {
             assign_kernel<<<ablocks, 256, 0, s>>>(emb, n, ix->cent, K, assign);
             if (it == iters) break;
-            cudaMemsetAsync(sums, 0, (size_t)K * D * 4, s);
+            cudaMemsetAsync(sums, 0, (size_t)K * D * 8, s);
             cudaMemsetAsync(counts, 0, (size_t)K * 4, s);
             accumulate_kernel<<<(unsigned)std::min<int64_t>((n + 7) / 8, 8192), 256, 0, s>>>(emb, n, assign, sums, counts);
             update_kernel<<<(unsigned)((K + 7) / 8), 256, 0, s>>>(sums, counts, K, ix->cent);
@@ -613,7 +555,6 @@ int ivf_build(const dt_encoder *enc, const uint64_t *d_db, int64_t n, int32_t n_
         delete ix;
         return rc;
     }
-    build_widened(ix, s);
     *out = ix;
     return DT_OK;
 }
@@ -624,7 +565,6 @@ void ivf_free(dt_ivf *ix)
     cudaDeviceSynchronize();
     cudaFree(ix->cent); cudaFree(ix->cent_t); cudaFree(ix->offsets); cudaFree(ix->db);
     cudaFree(ix->ids);
-    free_widened(ix);
     delete ix;
 }
 
@@ -700,12 +640,12 @@ int ivf_search(const dt_ivf *ix, const dt_encoder *enc, const uint64_t *d_q, int
     }
     const unsigned pb = (unsigned)std::min<int64_t>((pairs + 255) / 256, 8192);
     pair_count_kernel<<<pb, 256, 0, s>>>(probe, pairs, counts);
-    unit_plan_kernel<<<1, 1024, 0, s>>>(counts, ix->K, ix->offsets, ix->wbase, tile_base, units,
-                                        n_units, n_tiles);
+    unit_plan_kernel<<<1, 1024, 0, s>>>(counts, ix->K, ix->offsets, tile_base, units, n_units,
+                                        n_tiles);
     pair_scatter_kernel<<<pb, 256, 0, s>>>(probe, nq, n_probe, tile_base, fill, slot_q, slot_of);
     DT_CUDA_TRY(cudaGetLastError());
     int rc = launch_tc_units(ix->db, ix->n, ix->ids, d_q, slot_q, units, n_units, n_tiles,
-                             max_tiles, k, partial, s, ix->w_exp, ix->w_side);
+                             max_tiles, k, partial, s);
     if (rc == DT_OK) {
         pair_merge_kernel<<<(unsigned)((nq + 7) / 8), 256, 0, s>>>(partial, slot_of, n_probe, d_q,
                                                                    nq, k, d_idx, d_score);

@@ -88,7 +88,6 @@ __global__ void object_units_kernel(const int64_t *__restrict__ offsets, int n_o
     t.a_tile1 = two ? 2 * p + 1 : -1;
     t.nvalid1 = two ? (int32_t)std::min<int64_t>(kTcTileM, m - (int64_t)(2 * p + 1) * kTcTileM) : 0;
     t.out_base = (int64_t)o * slots_per_object;
-    t.tile0 = 0;
     units[u] = t;
 }
 

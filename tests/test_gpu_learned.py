@@ -218,3 +218,23 @@ def test_ivf_edges_on_both_paths():
             assert np.all(got[r, :m] < db.shape[0]) and np.all(np.isfinite(s1[r, :m]))
             assert np.all(got[r, m:] == 0xFFFFFFFF) and np.all(np.isinf(s1[r, m:]))
             assert np.all(np.diff(s1[r, :m]) >= 0)
+
+
+def test_ivf_build_is_the_same_on_every_run():
+    """The k-means sums are integers (fixed point), so two builds from the
+    same encoder and database make the same lists, and their searches return
+    the same results."""
+    enc = learned.Encoder(seed=23)
+    db = mixed_db(14, 40_000, per_object=800)
+    d_db = to_dev(db)
+    q, _ = synth.queries(15, db, 700)
+    d_q = to_dev(q)
+    runs = []
+    for _ in range(2):
+        ivf = learned.IVF(enc, d_db, n_lists=128, iters=5)
+        idx, score, _ = ivf.search(d_q, 5, 6, with_scanned=True, path=2)
+        runs.append((ivf.offsets(), idx.cpu().numpy(), score.cpu().numpy()))
+        ivf.free()
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert np.array_equal(runs[0][2], runs[1][2])
