@@ -303,8 +303,12 @@ ivf_search_kernel(const float *__restrict__ qemb, const uint64_t *__restrict__ q
 
 // Probes only, QB queries per block (QB <= 8): every centroid load feeds
 // QB dot products; then warp w chooses query w's n_probe lists from the
-// scores in shared memory by repeated warp-wide argmax (no block
-// barriers).  Scores, order and ties are those of ivf_search_kernel.
+// scores in shared memory (no block barriers).  Lane l holds the centroids
+// l, l + 32, ...; it keeps its four best (score, -index) keys in registers,
+// and the warp merges the lanes' sorted heads, one warp-wide maximum per
+// pick; a lane whose four have all been taken finds its next four below the
+// last one.  The picks and their order are those of a full warp-wide argmax
+// per pick, as in ivf_search_kernel.
 template <int QB>
 __global__ void __launch_bounds__(ST)
 ivf_probe_kernel(const float *__restrict__ qemb, int64_t nq, const float *__restrict__ cent, int K,
@@ -313,50 +317,106 @@ ivf_probe_kernel(const float *__restrict__ qemb, int64_t nq, const float *__rest
 {
     static_assert(QB <= ST / 32, "one warp per query");
     extern __shared__ float csc[];                   // [QB][K]
-    __shared__ float qe[QB][D];
+    __shared__ __align__(16) float qe[D][QB];        // dimension-major: a dimension's QB values together
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * QB;
     for (int i = tid; i < QB * D; i += ST) {
         const int64_t q = q0 + i / D;
-        qe[i / D][i % D] = q < nq ? qemb[q * D + i % D] : 0.f;
+        qe[i % D][i / D] = q < nq ? qemb[q * D + i % D] : 0.f;
     }
     __syncthreads();
-    for (int c = tid; c < K; c += ST) {
-        float sc[QB];
+    // a thread scores four adjacent centroids for the QB queries (4 x QB
+    // accumulators, one 16-byte load of centroid values per dimension when
+    // K is a multiple of 4); the loads run PF dimensions ahead of the FMAs
+    // (L2 latency).  Each score is the same FMA chain over the dimensions in
+    // order as in ivf_search_kernel.
+    constexpr int PF = 8;
+    static_assert(D % PF == 0, "whole prefetch groups");
+    const bool vec = (K & 3) == 0;
+    for (int c0 = 4 * tid; c0 < K; c0 += 4 * ST) {
+        auto load4 = [&](int d) {
+            const float *row = cent + (int64_t)d * K + c0;
+            if (vec) return __ldg(reinterpret_cast<const float4 *>(row));
+            return make_float4(__ldg(row), c0 + 1 < K ? __ldg(row + 1) : 0.f,
+                               c0 + 2 < K ? __ldg(row + 2) : 0.f, c0 + 3 < K ? __ldg(row + 3) : 0.f);
+        };
+        float sc[QB][4];
 #pragma unroll
-        for (int i = 0; i < QB; ++i) sc[i] = 0.f;
-        for (int d = 0; d < D; ++d) {
-            const float w = __ldg(cent + (int64_t)d * K + c);
+        for (int i = 0; i < QB; ++i)
 #pragma unroll
-            for (int i = 0; i < QB; ++i) sc[i] = fmaf(qe[i][d], w, sc[i]);
+            for (int j = 0; j < 4; ++j) sc[i][j] = 0.f;
+        float4 nx[PF];
+#pragma unroll
+        for (int e = 0; e < PF; ++e) nx[e] = load4(e);
+        for (int d0 = 0; d0 < D; d0 += PF) {
+            float4 cu[PF];
+#pragma unroll
+            for (int e = 0; e < PF; ++e) cu[e] = nx[e];
+            if (d0 + PF < D) {
+#pragma unroll
+                for (int e = 0; e < PF; ++e) nx[e] = load4(d0 + PF + e);
+            }
+#pragma unroll
+            for (int e = 0; e < PF; ++e) {
+                const float w[4] = {cu[e].x, cu[e].y, cu[e].z, cu[e].w};
+#pragma unroll
+                for (int i = 0; i < QB; ++i) {
+                    const float qv = qe[d0 + e][i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) sc[i][j] = fmaf(qv, w[j], sc[i][j]);
+                }
+            }
         }
 #pragma unroll
-        for (int i = 0; i < QB; ++i) csc[i * K + c] = sc[i];
+        for (int i = 0; i < QB; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (c0 + j < K) csc[i * K + c0 + j] = sc[i][j];
     }
     __syncthreads();
     const int64_t q = q0 + wid;
     if (wid >= QB || q >= nq) return;
-    float *sc = csc + (int64_t)wid * K;
+    const float *sc = csc + (int64_t)wid * K;
+    // key of centroid c: larger is better; every key is nonzero, so 0 marks
+    // an empty register slot
+    auto key_of = [&](int c) {
+        uint32_t fb = __float_as_uint(sc[c]);
+        fb = (fb & 0x80000000u) ? ~fb : (fb | 0x80000000u);
+        return ((unsigned long long)fb << 32) | (0xFFFFFFFFu - (uint32_t)c);
+    };
+    // this lane's four best keys below `below`, in descending order
+    unsigned long long t0, t1, t2, t3;
+    auto best4 = [&](unsigned long long below) {
+        t0 = t1 = t2 = t3 = 0ull;
+        for (int c = lane; c < K; c += 32) {
+            unsigned long long x = key_of(c);
+            if (x >= below || x <= t3) continue;
+            t3 = x;
+            if (t3 > t2) { x = t2; t2 = t3; t3 = x; }
+            if (t2 > t1) { x = t1; t1 = t2; t2 = x; }
+            if (t1 > t0) { x = t0; t0 = t1; t1 = x; }
+        }
+    };
+    best4(~0ull);
     int64_t rows = 0;
     for (int p = 0; p < n_probe; ++p) {
-        unsigned long long b = 0ull;
-        for (int c = lane; c < K; c += 32) {
-            uint32_t fb = __float_as_uint(sc[c]);
-            fb = (fb & 0x80000000u) ? ~fb : (fb | 0x80000000u);
-            const unsigned long long key = ((unsigned long long)fb << 32) | (0xFFFFFFFFu - (uint32_t)c);
-            b = key > b ? key : b;
-        }
+        unsigned long long b = t0;
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long u = __shfl_xor_sync(0xffffffffu, b, o);
             b = u > b ? u : b;
+        }
+        if (b == t0) {                 // this lane's head was taken (keys are distinct)
+            t0 = t1;
+            t1 = t2;
+            t2 = t3;
+            t3 = 0ull;
+            if (t0 == 0ull) best4(b);
         }
         const int c = (int)(0xFFFFFFFFu - (uint32_t)(b & 0xFFFFFFFFu));
         if (lane == 0) {
             probe_out[q * n_probe + p] = c;
             rows += offsets[c + 1] - offsets[c];
-            sc[c] = -INFINITY;
         }
-        __syncwarp();
     }
     if (lane == 0 && scanned) scanned[q] = rows;
 }

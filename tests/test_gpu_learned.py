@@ -238,3 +238,20 @@ def test_ivf_build_is_the_same_on_every_run():
     assert np.array_equal(runs[0][0], runs[1][0])
     assert np.array_equal(runs[0][1], runs[1][1])
     assert np.array_equal(runs[0][2], runs[1][2])
+
+
+@pytest.mark.parametrize("n_lists", [37, 130])
+def test_ivf_probe_kernel_on_list_counts_not_multiple_of_four(n_lists):
+    """The tensor path's probe kernel scores four centroids per thread with
+    vector loads only when the list count is a multiple of four; other counts
+    take scalar loads.  Its picks equal the per-query kernel's either way."""
+    enc = learned.Encoder(seed=24)
+    db = mixed_db(16, 12_000, per_object=400)
+    d_db = to_dev(db)
+    ivf = learned.IVF(enc, d_db, n_lists=n_lists, iters=3)
+    q, _ = synth.queries(17, db, 1500)
+    d_q = to_dev(q)
+    for n_probe in (1, 5, n_lists):
+        a = ivf.search(d_q, 3, n_probe, with_scanned=True, path=1)
+        b = ivf.search(d_q, 3, n_probe, with_scanned=True, path=2)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[2], b[2])
