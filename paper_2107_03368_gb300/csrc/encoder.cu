@@ -17,7 +17,8 @@
 // s_ij = <e_q[i], e_t[j]> / tau, is differentiated by hand back through
 // every layer; Adam updates the parameters.  Kernels are plain FP32 on CUDA
 // cores, one thread per output element (weight gradients split over the
-// batch with atomics).  Inference (enc_embed) runs on the tensor cores for
+// batch, the splits' partial sums added in a fixed order, so a step is the
+// same on every run).  Inference (enc_embed) runs on the tensor cores for
 // large batches (enc_tc.cu, BF16 operands); the FP32 inference path here is
 // one fused kernel over
 // weights re-laid out output-channel-contiguous: each thread keeps all
@@ -248,20 +249,45 @@ __global__ void fc_bwd_data(const float *__restrict__ dout, const float *__restr
     din[i] = s;
 }
 
-// dW[n][k] += sum_m dout[m][n] in[m][k]; db[n] += sum_m dout[m][n]
-// (batch split over blockIdx.y, partial sums added atomically)
+// The weight gradients sum over the batch, which is split over blockIdx.y
+// for parallelism.  Each split writes its partial sums to part[split][i]
+// and sum_partials adds them in split order, so that a training step gives
+// the same gradient on every run (atomic float additions would not).
+
+// part[y][n * (K + 1) + k] = sum over split y's rows m of dout[m][n] in[m][k]
+// (k < K), or of dout[m][n] (k = K, the bias)
 __global__ void fc_bwd_weight(const float *__restrict__ dout, const float *__restrict__ in, int M,
-                              int K, int N, int m_chunk, float *__restrict__ dW,
-                              float *__restrict__ db)
+                              int K, int N, int m_chunk, float *__restrict__ part)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)N * (K + 1)) return;
+    const int64_t count = (int64_t)N * (K + 1);
+    if (i >= count) return;
     const int n = (int)(i / (K + 1)), k = (int)(i % (K + 1));
     const int m0 = blockIdx.y * m_chunk, m1 = min(M, m0 + m_chunk);
     float s = 0.f;
     for (int m = m0; m < m1; ++m) s += dout[(int64_t)m * N + n] * (k < K ? in[(int64_t)m * K + k] : 1.f);
-    if (k < K) atomicAdd(&dW[(int64_t)n * K + k], s);
-    else atomicAdd(&db[n], s);
+    part[blockIdx.y * count + i] = s;
+}
+
+// g = sum over the ny splits of part[y][i], in split order, written to the
+// weight gradient (i < n_w: dw[i]) or the bias gradient (db[i - n_w]); for
+// a dense layer (fc_k > 0) i = n * (fc_k + 1) + k, the bias at k = fc_k.
+__global__ void sum_partials(const float *__restrict__ part, int ny, int64_t count, int fc_k,
+                             int64_t n_w, float *__restrict__ dw, float *__restrict__ db)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float s = 0.f;
+    for (int y = 0; y < ny; ++y) s += part[(int64_t)y * count + i];
+    if (fc_k > 0) {
+        const int64_t n = i / (fc_k + 1), k = i % (fc_k + 1);
+        if (k < fc_k) dw[n * fc_k + k] = s;
+        else db[n] = s;
+    } else if (i < n_w) {
+        dw[i] = s;
+    } else {
+        db[i - n_w] = s;
+    }
 }
 
 // da3 = pool^T(dp) * (a3 > 0)
@@ -307,12 +333,13 @@ __global__ void conv_bwd_data(const float *__restrict__ dout, const float *__res
     din[i] = s;
 }
 
-// dw[co][ci][ky][kx] += sum_{m,y,x} dout[m][co][y][x] in[m][ci][2y+ky-1][2x+kx-1]
-// db[co] += sum dout; the batch is split over blockIdx.y.  `in` is FP32
-// activations, or bits when `bits` is non-null (first layer).
+// part[y][i], for split y's rows m: i < Co Ci 9 the weight (co, ci, ky, kx),
+// sum over (m, y, x) of dout[m][co][y][x] in[m][ci][2y+ky-1][2x+kx-1]; above,
+// the bias co = i - Co Ci 9, sum of dout[m][co].  `in` is FP32 activations,
+// or bits when `bits` is non-null (first layer).
 __global__ void conv_bwd_weight(const float *__restrict__ dout, const float *__restrict__ in,
                                 const uint64_t *__restrict__ bits, int M, int Ci, int Hi, int Co,
-                                int Ho, int m_chunk, float *__restrict__ dw, float *__restrict__ db)
+                                int Ho, int m_chunk, float *__restrict__ part)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nw = (int64_t)Co * Ci * 9;
@@ -336,15 +363,14 @@ __global__ void conv_bwd_weight(const float *__restrict__ dout, const float *__r
                 }
             }
         }
-        atomicAdd(&dw[i], s);
     } else {
         const int co = (int)(i - nw);
         for (int m = m0; m < m1; ++m) {
             const float *g = dout + ((int64_t)m * Co + co) * Ho * Ho;
             for (int j = 0; j < Ho * Ho; ++j) s += g[j];
         }
-        atomicAdd(&db[co], s);
     }
+    part[blockIdx.y * (nw + Co) + i] = s;
 }
 
 __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m1,
@@ -755,19 +781,34 @@ int enc_train_step(dt_encoder *e, const uint64_t *d_q, const uint64_t *d_t, int3
     DT_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)NPARAM * 4, s));
     l2norm_bwd<<<blocks_for((int64_t)M * 32), 256, 0, s>>>(w.z, w.e, w.de, M, w.dz);
     const int mc = 64, gy = (M + mc - 1) / mc;
-    fc_bwd_weight<<<dim3(blocks_for((int64_t)F2 * (F1 + 1)), gy), 256, 0, s>>>(w.dz, w.h, M, F1, F2, mc,
-                                                                                 G + OWF2, G + OBF2);
+    const int cc = 8, gyc = (M + cc - 1) / cc;
+    // per-split partial sums of the weight gradients, reused layer by layer
+    Scratch gscratch(s);
+    float *part = nullptr;
+    const int64_t part_n = std::max({(int64_t)gy * F2 * (F1 + 1), (int64_t)gy * F1 * (F0 + 1),
+                                     (int64_t)gyc * (C3 * C2 * 9 + C3), (int64_t)gyc * (C2 * C1 * 9 + C2),
+                                     (int64_t)gyc * (C1 * 9 + C1)});
+    DT_CUDA_TRY(gscratch.alloc(&part, (size_t)part_n * 4));
+    auto fc_grad = [&](const float *dout, const float *in, int K, int N, float *dw, float *db) {
+        const int64_t count = (int64_t)N * (K + 1);
+        fc_bwd_weight<<<dim3(blocks_for(count), gy), 256, 0, s>>>(dout, in, M, K, N, mc, part);
+        sum_partials<<<blocks_for(count), 256, 0, s>>>(part, gy, count, K, 0, dw, db);
+    };
+    auto conv_grad = [&](const float *dout, const float *in, const uint64_t *bits, int Ci, int Hi, int Co,
+                         int Ho, float *dw, float *db) {
+        const int64_t nw = (int64_t)Co * Ci * 9, count = nw + Co;
+        conv_bwd_weight<<<dim3(blocks_for(count), gyc), 256, 0, s>>>(dout, in, bits, M, Ci, Hi, Co, Ho,
+                                                                     cc, part);
+        sum_partials<<<blocks_for(count), 256, 0, s>>>(part, gyc, count, 0, nw, dw, db);
+    };
+    fc_grad(w.dz, w.h, F1, F2, G + OWF2, G + OBF2);
     fc_bwd_data<<<blocks_for((int64_t)M * F1), 256, 0, s>>>(w.dz, P + OWF2, M, F1, F2, w.h, w.dh);
-    fc_bwd_weight<<<dim3(blocks_for((int64_t)F1 * (F0 + 1)), gy), 256, 0, s>>>(w.dh, w.p, M, F0, F1, mc,
-                                                                                 G + OWF1, G + OBF1);
+    fc_grad(w.dh, w.p, F0, F1, G + OWF1, G + OBF1);
     fc_bwd_data<<<blocks_for((int64_t)M * F0), 256, 0, s>>>(w.dh, P + OWF1, M, F0, F1, nullptr, w.dp);
     pool_bwd<<<blocks_for((int64_t)M * A3), 256, 0, s>>>(w.dp, w.a3, M, w.da3);
-    const int cc = 8, gyc = (M + cc - 1) / cc;
-    conv_bwd_weight<<<dim3(blocks_for((int64_t)C3 * C2 * 9 + C3), gyc), 256, 0, s>>>(
-        w.da3, w.a2, nullptr, M, C2, H2, C3, H3, cc, G + OW3, G + OB3);
+    conv_grad(w.da3, w.a2, nullptr, C2, H2, C3, H3, G + OW3, G + OB3);
     conv_bwd_data<<<blocks_for((int64_t)M * A2), 256, 0, s>>>(w.da3, P + OW3, M, C2, H2, C3, H3, w.a2, w.da2);
-    conv_bwd_weight<<<dim3(blocks_for((int64_t)C2 * C1 * 9 + C2), gyc), 256, 0, s>>>(
-        w.da2, w.a1, nullptr, M, C1, H1, C2, H2, cc, G + OW2, G + OB2);
+    conv_grad(w.da2, w.a1, nullptr, C1, H1, C2, H2, G + OW2, G + OB2);
     // conv1's input gradient is not needed; its output gradient da1 is:
     {
         // da1 = conv2^T(da2) * (a1 > 0), kept in a scratch region sized M * A1
@@ -781,8 +822,7 @@ int enc_train_step(dt_encoder *e, const uint64_t *d_q, const uint64_t *d_t, int3
         DT_CUDA_TRY(cudaMemcpyAsync(bits, d_q, (size_t)B * kWords * 8, cudaMemcpyDeviceToDevice, s));
         DT_CUDA_TRY(cudaMemcpyAsync(bits + (size_t)B * kWords, d_t, (size_t)B * kWords * 8,
                                     cudaMemcpyDeviceToDevice, s));
-        conv_bwd_weight<<<dim3(blocks_for((int64_t)C1 * 9 + C1), gyc), 256, 0, s>>>(
-            buf, nullptr, bits, M, 1, 64, C1, H1, cc, G + OW1, G + OB1);
+        conv_grad(buf, nullptr, bits, 1, 64, C1, H1, G + OW1, G + OB1);
     }
     DT_CUDA_TRY(cudaGetLastError());
     if (update) {

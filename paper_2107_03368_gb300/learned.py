@@ -152,16 +152,18 @@ class IVF:
 
 
 def train(enc: Encoder, d_db, make_queries, steps, batch=256, lr=1e-3, tau=0.05, log=None,
-          epochs_per_round=1):
+          epochs_per_round=1, seed=0):
     """Train on (query, exact nearest neighbour) pairs.
 
     make_queries(round) -> uint64 numpy [m, 64] new query descriptors; their
     exact nearest neighbours come from bf_search on d_db, and each round's
-    pairs are used for epochs_per_round passes (reshuffled).  Returns the
-    loss history."""
+    pairs are used for epochs_per_round passes (reshuffled by a generator
+    seeded with `seed`, so that the same inputs train the same weights).
+    Returns the loss history."""
     losses = []
     step = 0
     rnd = 0
+    rng = np.random.default_rng(seed)
     while step < steps:
         q = make_queries(rnd)
         rnd += 1
@@ -169,7 +171,7 @@ def train(enc: Encoder, d_db, make_queries, steps, batch=256, lr=1e-3, tau=0.05,
         nn, _, _ = dt.bf_search(d_db, d_q, 1)
         tgt = d_db[nn[:, 0].long()]
         for _ in range(epochs_per_round):
-            perm = torch.randperm(d_q.shape[0], device=d_q.device)
+            perm = torch.from_numpy(rng.permutation(d_q.shape[0])).to(d_q.device)
             for b0 in range(0, d_q.shape[0] - batch + 1, batch):
                 if step >= steps:
                     break

@@ -3,7 +3,8 @@
 - the encoder's forward kernels match the FP64 oracle;
 - the hand-written backward kernels give the oracle's gradient (every
   layer), and the loss value matches;
-- training steps lower the InfoNCE loss;
+- training steps lower the InfoNCE loss, and give the same weights on
+  every run;
 - the inverted-file search ranks candidates exactly: probing every list
   returns the exact top-k, and with few probes every answer that is found is
   the exact neighbour's distance or worse (never better than exact).
@@ -91,6 +92,25 @@ def test_training_lowers_the_loss():
     first = np.mean([l for _, l in hist[:1]])
     last = np.mean([l for _, l in hist[-2:]])
     assert last < 0.7 * first, hist
+
+
+def test_training_is_the_same_on_every_run():
+    """The weight gradients' batch splits are summed in a fixed order and the
+    shuffle is seeded, so two trainings from the same seed and data end with
+    the same weights, bit for bit."""
+    db, _ = synth.database(22, 8_000, per_object=400, pool=20)
+    d_db = to_dev(db)
+
+    def make_queries(r):
+        return synth.queries(2000 + r, db, 1024)[0]
+
+    params = []
+    for _ in range(2):
+        enc = learned.Encoder(seed=9)
+        learned.train(enc, d_db, make_queries, steps=12, batch=128, lr=2e-3, tau=0.1)
+        params.append(enc.get_params())
+        enc.free()
+    assert np.array_equal(params[0], params[1])
 
 
 @pytest.mark.parametrize("path", [1, 2])
